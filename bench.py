@@ -1,0 +1,329 @@
+"""Benchmark: sustained CG Gflops of the mixed-precision domain-wall solve on GB300.
+
+Workload: one full solve D psi = eta on a 16^3 x 32 lattice, Ns = 16, weights
+omega_s = sigma_s = 1 + 0.5 cos(pi (s - 1/2) / Ns), m0 = 1.8, mq = 0.02, links exp(0.5 i H)
+(seed 2), complex Gaussian source (seed 2); FP32 inner CG with FP64 reliable updates to a
+true relative residual of 1e-10.  One step = one whole solve (source preparation, inner
+CG, FP64 restarts, reconstruction, final FP64 residual check).
+
+value: counted flops (fixed per-site counts) / device time, inputs resident in HBM.
+e2e:   the same metric through dwf_solve with pinned host buffers (H2D of eta and D2H of
+       psi inside the timed region).
+The working set (~1.5 GB) is larger than L2, so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle on this machine's host cores instead (one
+C C^dagger application on the same lattice per step: a bounded sample of the workload).
+Multi-GPU (torchrun): every rank solves its own replica (no data-path collective);
+value = all ranks' flops / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS, NS, M0, MQ, EPS, SEED = (16, 16, 16, 32), 16, 1.8, 0.02, 0.5, 2
+WORKLOAD = "dwf_full_solve_16x16x16x32_Ns16_cosine_mq0.02_tol1e-10"
+METRIC = "CG Gflops & % HBM roofline (16^3x32,Ns16); served solves/s, p99 latency"
+PAPER_BEST_GFLOPS = 233.0  # GTX 480, CG (mixed), same lattice (Table 1): other hardware, context
+
+# ncu DRAM traffic per launch of the dominant kernel class, from profiles/ (bytes), keyed by
+# the kernel class; filled from the committed ncu summary of the current kernel source.
+NCU_TRAFFIC = {}
+
+
+def flops_ccdag(n, ns):
+    return n * (5232.0 + 192.0 * ns)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores: one FP64 C C^dag application per step."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+
+    import oracle
+    from paper_1101_0423_gb300 import inputs
+    oracle.build()
+    om, sg = inputs.weights("cosine", NS)
+    U = inputs.gauge_field(DIMS, EPS, seed=SEED)
+    x = inputs.gaussian_source(DIMS, NS, seed=SEED, parity=1)
+    mp, mm = oracle.m5(NS, M0, MQ, om, sg)
+    n = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2 * NS
+    for _ in range(args.warmup):
+        oracle.ccdag_op(DIMS, NS, U, mp, mm, 1, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.ccdag_op(DIMS, NS, U, mp, mm, 1, x)
+    dt = time.perf_counter() - t0
+    gf = args.steps * flops_ccdag(n, NS) / dt / 1e9
+    sample = f"{args.steps} FP64 C C^dagger applications on 16^3x32x16 (oracle, single thread)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": gf, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "C C^dagger application"},
+        "cpu_baseline": {"value": gf, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": gf, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def cpu_baseline_sample():
+    """Oracle timed on one host core on a bounded sample: one FP64 C C^dagger application."""
+    import oracle
+    from paper_1101_0423_gb300 import inputs
+    oracle.build()
+    om, sg = inputs.weights("cosine", NS)
+    U = inputs.gauge_field(DIMS, EPS, seed=SEED)
+    x = inputs.gaussian_source(DIMS, NS, seed=SEED, parity=1)
+    mp, mm = oracle.m5(NS, M0, MQ, om, sg)
+    n = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2 * NS
+    t0 = time.perf_counter()
+    oracle.ccdag_op(DIMS, NS, U, mp, mm, 1, x)
+    dt = time.perf_counter() - t0
+    return {"value": flops_ccdag(n, NS) / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": "one FP64 C C^dagger application on 16^3x32x16 (single thread), "
+                      f"{dt:.1f} s; same flop count as the GPU's CG iterations"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--inner", default="f32", choices=["f32", "f16", "bf16", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+
+    from paper_1101_0423_gb300 import build as _build
+    from paper_1101_0423_gb300 import dwf, inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        tdist.barrier()
+    dwf.load()
+    prec = {"f32": dwf.PREC_F32, "f16": dwf.PREC_F16, "bf16": dwf.PREC_BF16, "f64": dwf.PREC_F64}[args.inner]
+
+    om, sg = inputs.weights("cosine", NS)
+    U = inputs.gauge_field(DIMS, EPS, seed=SEED)
+    eta = inputs.gaussian_source(DIMS, NS, seed=SEED)
+    stream = torch.cuda.current_stream()
+    ctx = dwf.Context(DIMS, NS, M0, MQ, om, sg, U)
+    d_eta = torch.from_numpy(eta).cuda()
+    d_psi = torch.empty_like(d_eta)
+    params = dwf.dwf_solve_params_default()
+    params.tol = 1e-10
+    params.inner_prec = prec
+
+    def step(profile=0):
+        params.profile = profile
+        return dwf.dwf_solve_dev(ctx.h, d_eta, d_psi, params=params, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    flops = sum(s["flops"] for s in stats)
+    launches = sum(s["kernel_launches"] for s in stats)
+    t_max = ms
+    flops_all = flops
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        t_max = float(t.item())
+        f = torch.tensor([flops], device="cuda", dtype=torch.float64)
+        tdist.all_reduce(f)
+        flops_all = float(f.item())
+    value = flops_all / (t_max * 1e-3) / 1e9
+
+    # ---- e2e: through dwf_solve with pinned host buffers, copies inside the timed region
+    h_eta = torch.from_numpy(eta).pin_memory()
+    h_psi = torch.empty_like(h_eta).pin_memory()
+    import ctypes
+    lib = dwf.load()
+    P = ctypes.POINTER(ctypes.c_double)
+    pe = ctypes.cast(h_eta.data_ptr(), P)
+    pp = ctypes.cast(h_psi.data_ptr(), P)
+    params.profile = 0
+    barrier()
+    t0 = time.perf_counter()
+    e2e_flops = 0.0
+    for _ in range(args.steps):
+        st = dwf.SolveStats()
+        rc = lib.dwf_solve(ctx.h, pe, pp, ctypes.byref(params), ctypes.byref(st))
+        if rc != 0:
+            raise dwf.DwfError(rc, dwf.dwf_last_error(ctx.h))
+        e2e_flops += st.flops
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+        e2e_flops *= world
+    e2e_value = e2e_flops / e2e_s / 1e9
+    nbytes = eta.nbytes
+
+    # ---- roofline of the dominant kernel class: CUDA events around each launch on the
+    # library's launch stream, over profiled steps of the same workload
+    prof = [step(profile=1) for _ in range(max(1, min(args.steps, 2)))]
+    torch.cuda.synchronize()
+    n = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2 * NS
+    S = {0: 192, 1: 96, 2: 52, 3: 52}[prec]
+    G = {0: 144, 1: 72, 2: 24, 3: 24}[prec]
+    alg = {"hop_m5": 2 * S + 8 * G / NS, "hop_xpay": 3 * S + 8 * G / NS, "hop_update": 7 * S + 8 * G / NS,
+           "smix_p": 4 * S}
+    cls_ms = {k: sum(p["class_ms"][k] for p in prof) for k in dwf.KC_NAMES}
+    cls_n = {k: sum(p["class_launches"][k] for p in prof) for k in dwf.KC_NAMES}
+    total = sum(cls_ms.values())
+    dom = max(alg, key=lambda k: cls_ms[k])
+    avg_ms = cls_ms[dom] / max(cls_n[dom], 1)
+    achieved = alg[dom] * n / (avg_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = NCU_TRAFFIC.get(dom)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": f"k_hop ({dom})", "peak_source": peak_kind,
+                "bytes_per_launch": alg[dom] * n, "avg_launch_us": avg_ms * 1e3,
+                "class_share": {k: cls_ms[k] / total for k in cls_ms},
+                "class_frac": {k: (alg[k] * n / (cls_ms[k] / max(cls_n[k], 1) * 1e-3) / 1e9) / peak
+                               for k in alg if cls_n[k]}}
+
+    if rank != 0:
+        if world > 1:
+            tdist.destroy_process_group()
+        return
+    s0 = stats[-1]
+    out = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": value / PAPER_BEST_GFLOPS,
+        "dtype": {0: "f64", 1: "f32", 2: "f16", 3: "bf16"}[prec] + "+f64-restarts",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": "16x16x16x32", "Ns": NS, "weights": "cosine omega=sigma",
+                   "inner_prec": args.inner, "tol": 1e-10, "parallelism": f"replicas{world}",
+                   "l2": "working set > L2 (no flush needed)",
+                   "iters": s0["iters"], "restarts": s0["restarts"], "true_res": s0["true_res"],
+                   "true_res_full": s0["true_res_full"],
+                   "solves_per_s": world * args.steps / (t_max * 1e-3)},
+        "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "clocks": clocks,
+        "vs_baseline_note": "value / 233 Gflops (paper Table 1, GTX 480, same lattice): other hardware, context",
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_sample()
+    print(json.dumps(out))
+    ctx.close()
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * dwf.h -- C-ABI of the GB300 (sm_103a) even-odd preconditioned domain-wall fermion solver.
+ *
+ * The library applies and inverts the 5D domain-wall operator of Chiu, Hsieh, Mao, Ogawa,
+ * "GPU-Based Conjugate Gradient Solver for Lattice QCD with Domain-Wall Fermions"
+ * (Lattice 2010):
+ *
+ *   D(mq) = D_w (omega + sigma L) + (1 - L)                                   (Eq. 1, Eq. 5)
+ *   D_w   = Wilson operator with the -m0 term, d = 4                          (Eq. 2)
+ *   L     = P+ L+ + P- L-,  (L+)_{s,s-1} = 1, (L+)_{1,Ns} = -mq/(2 m0)        (Eq. 3-4)
+ *   M5    = [ (d - m0) + omega^{-1/2} (1 - L)(1 + cL)^{-1} omega^{-1/2} ]^{-1} (Eq. 8)
+ *   C     = 1 - M5 D_w^{p,1-p} M5 D_w^{1-p,p}  on Schur parity p              (Eq. 11)
+ *
+ * and solves C C^dagger x = b (Sec. 2.2) with a conjugate gradient (Algorithm 1) whose
+ * inner iterations run in FP32 (or 16-bit storage) and whose restarts recompute the true
+ * residual in FP64: reliable updates that keep the search direction, switching to defect
+ * correction (Algorithm 2) when reliable updates stop converging (Sec. 2.3).
+ *
+ * Conventions (readings of what the paper leaves open):
+ *   dims = {Nx, Ny, Nz, Nt}, every extent even and >= 2; periodic boundaries.
+ *   Host spinor layout (Sec. 3.1): real index c + 24 s + 24 Ns site with
+ *   site = x + Nx (y + Ny (z + Nz t)), c = reim + 2 (colour + 3 spin), s = 0..Ns-1.
+ *   A full 5D field holds 24 * Ns * Nx*Ny*Nz*Nt doubles.
+ *   Host gauge layout: U_mu(x)_{ab} at complex index ((site*4 + mu)*3 + a)*3 + b,
+ *   mu = 0..3 for x, y, z, t (72 doubles per site).
+ *   Gamma matrices: chiral basis, gamma_k = [[0, -i sigma_k], [i sigma_k, 0]],
+ *   gamma_4 = [[0, 1], [1, 0]], gamma_5 = gamma_1 gamma_2 gamma_3 gamma_4 = diag(1,1,-1,-1);
+ *   P+ acts on spins 0,1 and P- on spins 2,3.
+ *   Parity of a site: (x + y + z + t) mod 2, 0 = even, 1 = odd.  D_w^{EO} maps odd to
+ *   even sites, D_w^{OE} even to odd (block positions of Eq. 6).
+ *
+ * Ownership: the caller owns every host buffer and every device buffer it passes; the
+ * library copies in and out and never frees caller memory.  A dwf_ctx owns its device
+ * state (gauge copies, matrices, work vectors) and releases it in dwf_destroy.  A
+ * context is used by one host thread at a time; its calls are ordered on one CUDA stream.
+ *
+ * Errors: every call returns a dwf_status; nothing aborts and no exception crosses the
+ * boundary.  dwf_last_error(ctx) describes the last failure on that context.
+ */
+#ifndef DWF_H
+#define DWF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dwf_ctx dwf_ctx;
+
+typedef enum {
+    DWF_OK = 0,
+    DWF_EINVAL = 1,   /* invalid argument (odd extent, Ns < 1, omega_s <= 0, m0 outside (0,2), ...) */
+    DWF_ENOMEM = 2,   /* device or host allocation failed, or a budget would be exceeded */
+    DWF_ENOCONV = 3,  /* solver reached max_iter without meeting tol (stats still filled) */
+    DWF_EBUSY = 4,    /* no free slot (server) */
+    DWF_EAGAIN = 5,   /* poll: request not finished yet */
+    DWF_ETIMEOUT = 6, /* a bounded device-side wait gave up (kernel error word set) */
+    DWF_ECUDA = 7,    /* a CUDA runtime call failed; see dwf_last_error */
+    DWF_ENOGAUGE = 8  /* operator used before dwf_load_gauge */
+} dwf_status;
+
+/* operators of dwf_apply_eo */
+enum {
+    DWF_OP_DEO = 0,   /* out_even = D_w^{EO} in_odd   (Eq. 12, hopping term only) */
+    DWF_OP_DOE = 1,   /* out_odd  = D_w^{OE} in_even  (Eq. 12) */
+    DWF_OP_M5 = 2,    /* out_p = M5 in_p   (Eq. 8), on the sites of `parity` */
+    DWF_OP_M5T = 3,   /* out_p = M5^T in_p */
+    DWF_OP_C = 4,     /* out_p = C in_p    (Eq. 11) on Schur parity p = `parity` */
+    DWF_OP_CDAG = 5,  /* out_p = C^dagger in_p */
+    DWF_OP_CCDAG = 6, /* out_p = C C^dagger in_p */
+    DWF_OP_DFULL = 7, /* out = D(mq) in on the whole lattice (Eq. 1 / Eq. 5) */
+    DWF_OP_DW = 8     /* out = D_w in on every s-slice, whole lattice (Eq. 2) */
+};
+
+/* arithmetic of an operator application or of the inner CG */
+enum {
+    DWF_PREC_F64 = 0,  /* FP64 storage and arithmetic */
+    DWF_PREC_F32 = 1,  /* FP32 storage and arithmetic */
+    DWF_PREC_F16 = 2,  /* fp16 spinors with a per-(site,s) FP32 norm, 12-real fp16 links, FP32 arithmetic */
+    DWF_PREC_BF16 = 3  /* bf16 spinors with a per-(site,s) FP32 norm, 12-real bf16 links, FP32 arithmetic */
+};
+
+/* restart policy of the mixed-precision CG (Sec. 2.3) */
+enum {
+    DWF_MODE_AUTO = 0,     /* reliable updates; switch to defect correction if they stop converging */
+    DWF_MODE_RELIABLE = 1, /* keep p across restarts (reliable updates) */
+    DWF_MODE_DEFECT = 2    /* reset p := r at every restart (defect correction, Algorithm 2) */
+};
+
+/* which system dwf_solve solves */
+enum {
+    DWF_SYS_FULL = 0,   /* D psi = eta on the whole lattice, via Eq. 10 (source prep + CG + reconstruction) */
+    DWF_SYS_NORMAL = 1  /* C C^dagger x = b on the sites of schur_parity (the HMC use, Sec. 2.2) */
+};
+
+typedef struct {
+    double tol;        /* stop when |b - C C^dag x| <= tol |b| in FP64 (default 1e-10) */
+    double delta;      /* reliable-update trigger: restart when |r| < delta * max|r| since the
+                          last restart; <= 0 selects the default of the inner precision */
+    int max_iter;      /* cap on inner CG iterations (default 100000) */
+    int inner_prec;    /* DWF_PREC_* of the inner CG (default DWF_PREC_F32) */
+    int mode;          /* DWF_MODE_* (default DWF_MODE_AUTO) */
+    int system;        /* DWF_SYS_* (default DWF_SYS_FULL) */
+    int schur_parity;  /* parity of the Schur complement, 0 or 1 (default 1, the paper's odd sites) */
+    int check_every;   /* inner iterations between host polls of the device flags (default 8) */
+    int use_graph;     /* capture each batch of inner iterations in a CUDA graph (default 1) */
+    int profile;       /* record CUDA events around every kernel class (default 0) */
+    int reserved[6];
+} dwf_solve_params;
+
+/* kernel classes timed when params.profile != 0 */
+enum {
+    DWF_KC_HOP_M5 = 0,     /* inner hop + M5 epilogue (t = M5^T D w, u = M5 D q) */
+    DWF_KC_HOP_XPAY = 1,   /* inner hop + (p - g5 D t) epilogue + norm */
+    DWF_KC_HOP_UPDATE = 2, /* inner hop + M5 + CG update (r, x) + norm */
+    DWF_KC_SMIX_P = 3,     /* inner p = r + beta p and w = M5^T g5 p */
+    DWF_KC_F64 = 4,        /* FP64 restart operator, source preparation, reconstruction */
+    DWF_KC_OTHER = 5,      /* packing, conversions, norms */
+    DWF_KC_COUNT = 6
+};
+
+typedef struct {
+    int iters;             /* inner CG iterations */
+    int restarts;          /* FP64 true-residual recomputations */
+    int mode_used;         /* DWF_MODE_RELIABLE or DWF_MODE_DEFECT at the end */
+    int converged;         /* 1 when true_res <= tol */
+    double true_res;       /* |b - C C^dag x| / |b| in FP64 */
+    double true_res_full;  /* |eta - D psi| / |eta| in FP64 (DWF_SYS_FULL only, else 0) */
+    double flops;          /* counted flops (fixed per-site counts, see the design notes) */
+    double time_ms;        /* device time of the whole call, CUDA events on its stream */
+    double class_ms[DWF_KC_COUNT];   /* per kernel class, when profiling */
+    int class_launches[DWF_KC_COUNT];
+    long long kernel_launches;       /* kernels this call launched (graph nodes included) */
+    double bytes_hop_m5;             /* algorithmic bytes of one DWF_KC_HOP_M5 launch */
+    double reserved[3];
+} dwf_solve_stats;
+
+/* Fill p with the defaults listed above. */
+void dwf_solve_params_default(dwf_solve_params *p);
+
+/* Create a context for one lattice and one set of 5th-dimension parameters (Eq. 1-4).
+ * dims: host array {Nx,Ny,Nz,Nt}; Ns >= 1 and <= 64; 0 < m0 < 2; mq >= 0;
+ * omega, sigma: host arrays of Ns doubles, omega_s > 0 (copied).  Uses the current
+ * CUDA device.  On success *out receives the context. */
+dwf_status dwf_create(const int dims[4], int Ns, double m0, double mq, const double *omega,
+                      const double *sigma, dwf_ctx **out);
+
+/* Release every device and host resource of ctx (NULL is accepted). */
+dwf_status dwf_destroy(dwf_ctx *ctx);
+
+/* Load the gauge field from a host array in the host gauge layout (72 * V4 doubles).
+ * The links must be SU(3) for the 12-real 16-bit form to be exact. */
+dwf_status dwf_load_gauge(dwf_ctx *ctx, const double *U);
+/* Same from a device array (caller-owned, host gauge layout), ordered on `stream`
+ * (a cudaStream_t; NULL = the context's stream). */
+dwf_status dwf_load_gauge_dev(dwf_ctx *ctx, const double *d_U, void *stream);
+
+/* Apply operator `op` (DWF_OP_*) in precision `prec` (DWF_PREC_*) to a full-lattice host
+ * array `in` (24*Ns*V4 doubles, host layout) and write the full-lattice host array
+ * `out`.  Only the sites the operator reads are used from `in`; every site the
+ * operator does not write is set to 0 in `out`.  `parity` is the Schur parity for
+ * M5/M5T/C/CDAG/CCDAG and is ignored otherwise.  in and out must not overlap. */
+dwf_status dwf_apply_eo(dwf_ctx *ctx, int op, int prec, int parity, const double *in, double *out);
+/* Same with caller-owned device arrays in the host layout, ordered on `stream`. */
+dwf_status dwf_apply_eo_dev(dwf_ctx *ctx, int op, int prec, int parity, const double *d_in,
+                            double *d_out, void *stream);
+
+/* Solve.  DWF_SYS_FULL: rhs = eta, sol = psi (full-lattice host arrays) with D psi = eta.
+ * DWF_SYS_NORMAL: rhs = b, sol = x on the sites of params->schur_parity with
+ * C C^dag x = b (other sites of sol are set to 0).  params may be NULL (defaults);
+ * stats may be NULL.  Returns DWF_ENOCONV (with stats filled and the best x written)
+ * when max_iter is reached first. */
+dwf_status dwf_solve(dwf_ctx *ctx, const double *rhs, double *sol, const dwf_solve_params *params,
+                     dwf_solve_stats *stats);
+/* Same with caller-owned device arrays, ordered on `stream`. */
+dwf_status dwf_solve_dev(dwf_ctx *ctx, const double *d_rhs, double *d_sol,
+                         const dwf_solve_params *params, dwf_solve_stats *stats, void *stream);
+
+/* Text of the last error on ctx ("" if none); valid until the next call on ctx. */
+const char *dwf_last_error(const dwf_ctx *ctx);
+/* Name of a status code. */
+const char *dwf_status_string(dwf_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DWF_H */

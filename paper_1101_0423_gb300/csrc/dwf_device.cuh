@@ -1,0 +1,274 @@
+// dwf_device.cuh -- device code of the domain-wall solver for sm_103a.
+//
+// Data layout in HBM (one parity of the 4D lattice at a time; cb = checkerboard index of
+// a site within its parity, cb = site / 2 with site = x + Nx (y + Ny (z + Nz t))):
+//   spinor (Sec. 3.1 "Vector Index Conversion", re-derived for 16-byte loads):
+//     chunk k of (cb, s) at element ((cb * NCH + k) * Ns + s) of 16-byte chunks, so the
+//     Ns threads of one site read consecutive 16 bytes for every chunk;
+//     F64: 12 chunks of double2, F32: 6 chunks of float4, F16/BF16: 3 chunks of 8
+//     halves plus a per-(cb, s) FP32 norm at nrm[cb * Ns + s].
+//     Inside a (cb, s) the 24 reals keep the host order c = reim + 2 (colour + 3 spin).
+//   gauge, doubled per output parity: G[p][cb][dir][*] with dir 0..3 = U_mu(x) and
+//     dir 4..7 = U_mu(x - mu)^dagger (stored daggered), 18 reals (F64/F32) or the first
+//     two rows, 12 reals (F16/BF16; the third row is rebuilt as conj(row0 x row1)).
+//   neighbours: nbr[p][cb][dir] = cb of x + mu (dir < 4) / x - mu (dir >= 4) in parity 1-p.
+//
+// The hopping term of Eq. 12 is evaluated as H = sum_mu [(1 - g_mu) U psi(x+mu) +
+// (1 + g_mu) U^dag psi(x-mu)] with D = -H/2.  In the chiral basis g_mu = [[0, A],[A^dag, 0]]
+// so (1 + S g_mu) psi = (h, S A^dag h) with h = psi_up + S A psi_dn: the link multiplies
+// only the projected 2-spinor h (the spin-projection trick of Sec. 3.2) and the lower two
+// spins are rebuilt from U h.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dwf {
+
+enum { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3 };
+
+template <int P> struct PT;
+template <> struct PT<P_F64> {
+  using real = double; using chunk = double2; using lreal = double;
+  static constexpr int NCH = 12, RPC = 2, LREALS = 18; static constexpr bool HALF = false;
+};
+template <> struct PT<P_F32> {
+  using real = float; using chunk = float4; using lreal = float;
+  static constexpr int NCH = 6, RPC = 4, LREALS = 18; static constexpr bool HALF = false;
+};
+template <> struct PT<P_F16> {
+  using real = float; using chunk = uint4; using lreal = __half;
+  static constexpr int NCH = 3, RPC = 8, LREALS = 12; static constexpr bool HALF = true;
+};
+template <> struct PT<P_BF16> {
+  using real = float; using chunk = uint4; using lreal = __nv_bfloat16;
+  static constexpr int NCH = 3, RPC = 8, LREALS = 12; static constexpr bool HALF = true;
+};
+
+struct Field {
+  void *v;
+  float *nrm;  // 16-bit precisions only
+};
+
+// scalars of one CG solve, resident in device memory (FP64 throughout)
+struct CGScalars {
+  double rr;       // |r|^2 of the current inner residual
+  double rr_old;   // previous |r|^2 (denominator of beta)
+  double qq;       // |C^dag p|^2 = (p, C C^dag p)
+  double beta;     // p = r + beta p
+  double rmax2;    // max |r|^2 since the last restart
+  double delta2;   // reliable-update threshold squared
+  double target2;  // (tol |b|)^2
+  double red;      // result slot of plain norm reductions
+  double red2;
+  int restart_flag;  // set on device when an FP64 restart is due; kernels then skip work
+  int iter;          // inner iterations done
+  int iter_cap;      // restart when iter reaches this
+  int error;         // kernel error word (bounded wait gave up)
+};
+
+// ------------------------------------------------------------------ spinor access
+
+template <int P>
+__device__ __forceinline__ void load_sp(const Field f, long cb, int s, int Ns,
+                                        typename PT<P>::real (&o)[24]) {
+  using T = PT<P>;
+  const typename T::chunk *b = (const typename T::chunk *)f.v + (size_t)cb * T::NCH * Ns + s;
+  if constexpr (P == P_F64) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) { double2 c = b[(size_t)k * Ns]; o[2 * k] = c.x; o[2 * k + 1] = c.y; }
+  } else if constexpr (P == P_F32) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float4 c = b[(size_t)k * Ns];
+      o[4 * k] = c.x; o[4 * k + 1] = c.y; o[4 * k + 2] = c.z; o[4 * k + 3] = c.w;
+    }
+  } else {
+    const float nm = f.nrm[(size_t)cb * Ns + s];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 c = b[(size_t)k * Ns];
+      uint32_t w[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float2 v;
+        if constexpr (P == P_F16) v = __half22float2(*reinterpret_cast<__half2 *>(&w[j]));
+        else v = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&w[j]));
+        o[8 * k + 2 * j] = v.x * nm;
+        o[8 * k + 2 * j + 1] = v.y * nm;
+      }
+    }
+  }
+}
+
+// read-only variant for kernel inputs that no thread writes during the launch
+template <int P>
+__device__ __forceinline__ void load_sp_ro(const Field f, long cb, int s, int Ns,
+                                           typename PT<P>::real (&o)[24]) {
+  using T = PT<P>;
+  const typename T::chunk *b = (const typename T::chunk *)f.v + (size_t)cb * T::NCH * Ns + s;
+  if constexpr (P == P_F64) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) { double2 c = __ldg(b + (size_t)k * Ns); o[2 * k] = c.x; o[2 * k + 1] = c.y; }
+  } else if constexpr (P == P_F32) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float4 c = __ldg(b + (size_t)k * Ns);
+      o[4 * k] = c.x; o[4 * k + 1] = c.y; o[4 * k + 2] = c.z; o[4 * k + 3] = c.w;
+    }
+  } else {
+    const float nm = __ldg(f.nrm + (size_t)cb * Ns + s);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 c = __ldg(b + (size_t)k * Ns);
+      uint32_t w[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float2 v;
+        if constexpr (P == P_F16) v = __half22float2(*reinterpret_cast<__half2 *>(&w[j]));
+        else v = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&w[j]));
+        o[8 * k + 2 * j] = v.x * nm;
+        o[8 * k + 2 * j + 1] = v.y * nm;
+      }
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void store_sp(Field f, long cb, int s, int Ns,
+                                         const typename PT<P>::real (&v)[24]) {
+  using T = PT<P>;
+  typename T::chunk *b = (typename T::chunk *)f.v + (size_t)cb * T::NCH * Ns + s;
+  if constexpr (P == P_F64) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) b[(size_t)k * Ns] = make_double2(v[2 * k], v[2 * k + 1]);
+  } else if constexpr (P == P_F32) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      b[(size_t)k * Ns] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+  } else {
+    float mx = 0.f;
+#pragma unroll
+    for (int c = 0; c < 24; ++c) mx = fmaxf(mx, fabsf(v[c]));
+    const float sc = mx > 0.f ? 1.0f / mx : 0.f;
+    f.nrm[(size_t)cb * Ns + s] = mx;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint32_t w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float a = v[8 * k + 2 * j] * sc, bb = v[8 * k + 2 * j + 1] * sc;
+        if constexpr (P == P_F16) { __half2 h = __floats2half2_rn(a, bb); w[j] = *reinterpret_cast<uint32_t *>(&h); }
+        else { __nv_bfloat162 h = __floats2bfloat162_rn(a, bb); w[j] = *reinterpret_cast<uint32_t *>(&h); }
+      }
+      b[(size_t)k * Ns] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ links
+
+template <int P>
+__device__ __forceinline__ void load_link(const typename PT<P>::lreal *L, typename PT<P>::real (&W)[18]) {
+  if constexpr (!PT<P>::HALF) {
+#pragma unroll
+    for (int i = 0; i < 18; ++i) W[i] = L[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      if constexpr (P == P_F16) W[i] = __half2float(L[i]);
+      else W[i] = __bfloat162float(L[i]);
+    }
+    // third row = conj(row0 x row1) for an SU(3) matrix
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+      // (r0 x r1)_b = r0_{b1} r1_{b2} - r0_{b2} r1_{b1}
+      float re = (W[2 * b1] * W[6 + 2 * b2] - W[2 * b1 + 1] * W[6 + 2 * b2 + 1]) -
+                 (W[2 * b2] * W[6 + 2 * b1] - W[2 * b2 + 1] * W[6 + 2 * b1 + 1]);
+      float im = (W[2 * b1] * W[6 + 2 * b2 + 1] + W[2 * b1 + 1] * W[6 + 2 * b2]) -
+                 (W[2 * b2] * W[6 + 2 * b1 + 1] + W[2 * b2 + 1] * W[6 + 2 * b1]);
+      W[12 + 2 * b] = re;
+      W[12 + 2 * b + 1] = -im;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ spin projection
+
+// A_mu = upper-right block of gamma_mu; each row of A and A^dag has one non-zero
+// entry, phase code 0: 1, 1: i, 2: -1, 3: -i.
+__host__ __device__ constexpr int a_col(int mu, int j) { return (mu == 0 || mu == 1) ? 1 - j : j; }
+__host__ __device__ constexpr int a_ph(int mu, int j) {
+  return mu == 0 ? 3 : mu == 1 ? (j == 0 ? 2 : 0) : mu == 2 ? (j == 0 ? 3 : 1) : 0;
+}
+__host__ __device__ constexpr int ad_col(int mu, int k) { return (mu == 0 || mu == 1) ? 1 - k : k; }
+__host__ __device__ constexpr int ad_ph(int mu, int k) {
+  return mu == 0 ? 1 : mu == 1 ? (k == 0 ? 0 : 2) : mu == 2 ? (k == 0 ? 1 : 3) : 0;
+}
+
+template <int PH, typename R>
+__device__ __forceinline__ void phase(R &re, R &im) {
+  if constexpr (PH == 1) { R t = re; re = -im; im = t; }
+  else if constexpr (PH == 2) { re = -re; im = -im; }
+  else if constexpr (PH == 3) { R t = re; re = im; im = -t; }
+}
+
+// h_j = psi_j + S (A psi_dn)_j for the projected 2-spinor row j (colour a)
+template <int MU, int S, int J, typename R>
+__device__ __forceinline__ void project_row(R (&h)[2][3][2], const R (&ps)[24], int a) {
+  constexpr int src = 2 + a_col(MU, J);
+  R vr = ps[2 * (a + 3 * src)], vi = ps[2 * (a + 3 * src) + 1];
+  phase<a_ph(MU, J)>(vr, vi);
+  h[J][a][0] = ps[2 * (a + 3 * J)] + S * vr;
+  h[J][a][1] = ps[2 * (a + 3 * J) + 1] + S * vi;
+}
+
+// lower spin 2+K of (1 + S g_mu) applied to the upper result: S (A^dag wh)_K
+template <int MU, int S, int K, typename R>
+__device__ __forceinline__ void rebuild_row(R (&acc)[24], const R (&wh)[2][3][2], int a) {
+  R vr = wh[ad_col(MU, K)][a][0], vi = wh[ad_col(MU, K)][a][1];
+  phase<ad_ph(MU, K)>(vr, vi);
+  acc[2 * (a + 3 * (2 + K))] += S * vr;
+  acc[2 * (a + 3 * (2 + K)) + 1] += S * vi;
+}
+
+// acc += (1 + S g_mu) W psi,  S = -1 (forward, 1 - g) or +1 (backward, 1 + g)
+template <int MU, int S, typename R>
+__device__ __forceinline__ void hop_dir(R (&acc)[24], const R (&ps)[24], const R (&W)[18]) {
+  R h[2][3][2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    project_row<MU, S, 0>(h, ps, a);
+    project_row<MU, S, 1>(h, ps, a);
+  }
+  R wh[2][3][2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      R re = 0, im = 0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const R ur = W[2 * (3 * a + b)], ui = W[2 * (3 * a + b) + 1];
+        re += ur * h[j][b][0] - ui * h[j][b][1];
+        im += ur * h[j][b][1] + ui * h[j][b][0];
+      }
+      wh[j][a][0] = re;
+      wh[j][a][1] = im;
+    }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      acc[2 * (a + 3 * j)] += wh[j][a][0];
+      acc[2 * (a + 3 * j) + 1] += wh[j][a][1];
+    }
+    rebuild_row<MU, S, 0>(acc, wh, a);
+    rebuild_row<MU, S, 1>(acc, wh, a);
+  }
+}
+
+}  // namespace dwf

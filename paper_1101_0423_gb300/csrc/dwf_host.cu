@@ -1,0 +1,1158 @@
+// dwf_host.cu -- C-ABI entry points: context, gauge, operator applications, solver.
+//
+// The host does the flow control (Sec. 3: "CPU (host) is used to do the flow control,
+// memory assignment, and device control"); every vector operation, reduction and
+// operator application runs in the kernels of dwf_kernels.cuh.  The CG scalars
+// (alpha, beta, |r|^2, restart flag) stay on the device; the host reads them once per
+// batch of inner iterations, and a batch is replayed from a CUDA graph.
+#include <math.h>
+#include <stdio.h>
+
+#include <cmath>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "dwf_internal.h"
+
+using namespace dwf;
+
+namespace {
+
+constexpr double kD = 4.0;  // space-time dimension d of Eq. 2
+
+const char *status_name(dwf_status s) {
+  switch (s) {
+    case DWF_OK: return "DWF_OK";
+    case DWF_EINVAL: return "DWF_EINVAL";
+    case DWF_ENOMEM: return "DWF_ENOMEM";
+    case DWF_ENOCONV: return "DWF_ENOCONV";
+    case DWF_EBUSY: return "DWF_EBUSY";
+    case DWF_EAGAIN: return "DWF_EAGAIN";
+    case DWF_ETIMEOUT: return "DWF_ETIMEOUT";
+    case DWF_ECUDA: return "DWF_ECUDA";
+    case DWF_ENOGAUGE: return "DWF_ENOGAUGE";
+  }
+  return "DWF_UNKNOWN";
+}
+
+dwf_status fail(dwf_ctx *c, dwf_status st, const std::string &msg) {
+  if (c) c->err = std::string(status_name(st)) + ": " + msg;
+  return st;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? DWF_ENOMEM : DWF_ECUDA,          \
+                  std::string(#call) + " -> " + cudaGetErrorString(e_));                \
+  } while (0)
+
+#define TRY(expr)                        \
+  do {                                   \
+    dwf_status s_ = (expr);              \
+    if (s_ != DWF_OK) return s_;         \
+  } while (0)
+
+size_t site_bytes(int prec) { return prec == P_F64 ? 192 : prec == P_F32 ? 96 : 48; }
+int mat_index(int prec) { return prec == P_F64 ? 0 : 1; }
+bool valid_prec(int p) { return p >= DWF_PREC_F64 && p <= DWF_PREC_BF16; }
+
+// ------------------------------------------------------------------ fifth-dimension matrices
+//
+// M5 of Eq. 8 is applied as a dense Ns x Ns matrix per chirality (Sec. 3.3).  Its entries
+// are computed here column by column from the structure of Eq. 8: with y = omega^{-1/2} u
+// and z = (1 + cL)^{-1} y, M5^{-1} u = v becomes the cyclic bidiagonal system
+//   [(d - m0) sqrt(omega) + 1/sqrt(omega)] z + [(d - m0) sigma/sqrt(omega) - 1/sqrt(omega)] L z = v,
+// then u = sqrt(omega) (z + c L z).  L = L+ (chirality +) or L- (chirality -), Eq. 4.
+
+// (A + B L) z = v for the cyclic shift L of Eq. 4: chirality 0 uses L+ ((L z)_s = z_{s-1},
+// (L z)_0 = kappa z_{Ns-1}), chirality 1 uses L- = L+^T.  Returns false on a zero pivot.
+bool cyclic_solve(int Ns, const double *A, const double *B, double kappa, int chi, const double *v,
+                  double *z) {
+  std::vector<double> al(Ns), be(Ns);
+  auto at = [&](int k) { return chi == 0 ? k : Ns - 1 - k; };
+  const int s0 = at(0), last = at(Ns - 1);
+  al[s0] = 0.0;
+  be[s0] = 1.0;
+  for (int k = 1; k < Ns; ++k) {
+    const int s = at(k), sp = at(k - 1);
+    if (A[s] == 0.0) return false;
+    al[s] = (v[s] - B[s] * al[sp]) / A[s];
+    be[s] = -B[s] * be[sp] / A[s];
+  }
+  const double den = A[s0] + B[s0] * kappa * be[last];
+  if (den == 0.0) return false;
+  const double zeta = (v[s0] - B[s0] * kappa * al[last]) / den;
+  for (int s = 0; s < Ns; ++s) z[s] = al[s] + be[s] * zeta;
+  return true;
+}
+
+// (L z)_s for chirality chi
+double lshift(int Ns, double kappa, int chi, const double *z, int s) {
+  if (chi == 0) return s > 0 ? z[s - 1] : kappa * z[Ns - 1];
+  return s < Ns - 1 ? z[s + 1] : kappa * z[0];
+}
+
+bool build_matrices(dwf_ctx *c) {
+  const int Ns = c->Ns;
+  const double kappa = -c->mq / (2.0 * c->m0);
+  const double dm = kD - c->m0;
+  for (auto &m : c->mat) m.assign((size_t)2 * Ns * Ns, 0.0);
+  std::vector<double> A(Ns), B(Ns), A1(Ns), Bc(Ns), v(Ns), z(Ns);
+  for (int s = 0; s < Ns; ++s) {
+    const double rw = sqrt(c->omega[s]);
+    A[s] = dm * rw + 1.0 / rw;
+    B[s] = dm * c->sigma[s] / rw - 1.0 / rw;
+    A1[s] = 1.0;
+    Bc[s] = c->sigma[s] / c->omega[s];
+  }
+  for (int chi = 0; chi < 2; ++chi) {
+    double *M5 = c->mat[MK_M5].data() + (size_t)chi * Ns * Ns;
+    double *M5T = c->mat[MK_M5T].data() + (size_t)chi * Ns * Ns;
+    double *S1 = c->mat[MK_S1].data() + (size_t)chi * Ns * Ns;
+    double *S2 = c->mat[MK_S2].data() + (size_t)chi * Ns * Ns;
+    double *W = c->mat[MK_W].data() + (size_t)chi * Ns * Ns;
+    double *Z = c->mat[MK_Z].data() + (size_t)chi * Ns * Ns;
+    double *ID = c->mat[MK_ID].data() + (size_t)chi * Ns * Ns;
+    double *MS = c->mat[MK_MASS].data() + (size_t)chi * Ns * Ns;
+    for (int j = 0; j < Ns; ++j) {
+      std::fill(v.begin(), v.end(), 0.0);
+      v[j] = 1.0;
+      // column j of M5
+      if (!cyclic_solve(Ns, A.data(), B.data(), kappa, chi, v.data(), z.data())) return false;
+      for (int s = 0; s < Ns; ++s)
+        M5[s * Ns + j] = sqrt(c->omega[s]) * (z[s] + Bc[s] * lshift(Ns, kappa, chi, z.data(), s));
+      // column j of (1 + cL)^{-1}, for S2 = Y^{-1} sqrt(omega) = (1 + cL)^{-1} omega^{-1/2} (Eq. 9)
+      if (!cyclic_solve(Ns, A1.data(), Bc.data(), kappa, chi, v.data(), z.data())) return false;
+      for (int s = 0; s < Ns; ++s) S2[s * Ns + j] = z[s] / sqrt(c->omega[j]);
+    }
+    for (int s = 0; s < Ns; ++s)
+      for (int t = 0; t < Ns; ++t) {
+        M5T[s * Ns + t] = M5[t * Ns + s];
+        S1[s * Ns + t] = M5[s * Ns + t] / sqrt(c->omega[t]);  // S1 = M5 omega^{-1/2}
+        // L_{st} of Eq. 4 for this chirality
+        double Lst;
+        if (chi == 0) Lst = (s > 0 ? (t == s - 1) : (t == Ns - 1) * kappa);
+        else Lst = (s < Ns - 1 ? (t == s + 1) : (t == 0) * kappa);
+        if (Ns == 1) Lst = kappa;
+        const double diag = (s == t) ? 1.0 : 0.0;
+        W[s * Ns + t] = c->omega[s] * diag + c->sigma[s] * Lst;  // omega + sigma L
+        Z[s * Ns + t] = dm * W[s * Ns + t] + diag - Lst;          // (d - m0) W + 1 - L
+        ID[s * Ns + t] = diag;
+        MS[s * Ns + t] = dm * diag;
+      }
+  }
+  for (auto &m : c->mat)
+    for (double x : m)
+      if (!std::isfinite(x)) return false;
+  return true;
+}
+
+// ------------------------------------------------------------------ buffers
+
+dwf_status get_buf(dwf_ctx *c, const std::string &name, int prec, Field *f) {
+  const size_t n = (size_t)c->h * c->Ns;
+  const size_t bytes = n * site_bytes(prec);
+  const std::string key = name + "#" + std::to_string(prec);
+  Buf &b = c->bufs[key];
+  if (!b.v) {
+    CK(cudaMalloc(&b.v, bytes));
+    b.bytes = bytes;
+    if (prec >= P_F16) CK(cudaMalloc((void **)&b.nrm, n * sizeof(float)));
+    CK(cudaMemsetAsync(b.v, 0, bytes, c->stream));
+    if (b.nrm) CK(cudaMemsetAsync(b.nrm, 0, n * sizeof(float), c->stream));
+    CK(cudaStreamSynchronize(c->stream));  // ordered before any use on another stream
+  }
+  f->v = b.v;
+  f->nrm = b.nrm;
+  return DWF_OK;
+}
+
+dwf_status get_raw(dwf_ctx *c, const std::string &name, size_t bytes, void **p) {
+  Buf &b = c->bufs["raw:" + name];
+  if (b.v && b.bytes < bytes) {
+    cudaFree(b.v);
+    b.v = nullptr;
+  }
+  if (!b.v) {
+    CK(cudaMalloc(&b.v, bytes));
+    b.bytes = bytes;
+  }
+  *p = b.v;
+  return DWF_OK;
+}
+
+Geom geom(const dwf_ctx *c) {
+  Geom g;
+  for (int i = 0; i < 4; ++i) g.d[i] = c->dims[i];
+  g.h = c->h;
+  g.Ns = c->Ns;
+  return g;
+}
+
+// ------------------------------------------------------------------ launches (counted, optionally timed)
+
+cudaEvent_t next_event(dwf_ctx *c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_used++];
+}
+
+struct Timed {
+  dwf_ctx *c;
+  cudaStream_t st;
+  int cls;
+  cudaEvent_t a = nullptr;
+  Timed(dwf_ctx *c_, cudaStream_t st_, int cls_) : c(c_), st(st_), cls(cls_) {
+    if (c->profiling) {
+      a = next_event(c);
+      cudaEventRecord(a, st);
+    }
+    c->launches++;
+  }
+  ~Timed() {
+    if (c->profiling) {
+      cudaEvent_t b = next_event(c);
+      cudaEventRecord(b, st);
+      c->prof.push_back({cls, a, b});
+    }
+  }
+};
+
+cudaError_t hop_any(int prec, int epi, const HopArgs &a, cudaStream_t st) {
+  switch (prec) {
+    case P_F64: return hop_launch<P_F64>(epi, a, st);
+    case P_F32: return hop_launch<P_F32>(epi, a, st);
+    case P_F16: return hop_launch<P_F16>(epi, a, st);
+    case P_BF16: return hop_launch<P_BF16>(epi, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t smix_any(int prec, int mode, const SmixArgs &a, cudaStream_t st) {
+  switch (prec) {
+    case P_F64: return smix_launch<P_F64>(mode, a, st);
+    case P_F32: return smix_launch<P_F32>(mode, a, st);
+    case P_F16: return smix_launch<P_F16>(mode, a, st);
+    case P_BF16: return smix_launch<P_BF16>(mode, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t norm2_any(int prec, const VecArgs &v, int sm, cudaStream_t st) {
+  switch (prec) {
+    case P_F64: return norm2_launch<P_F64>(v, sm, st);
+    case P_F32: return norm2_launch<P_F32>(v, sm, st);
+    case P_F16: return norm2_launch<P_F16>(v, sm, st);
+    case P_BF16: return norm2_launch<P_BF16>(v, sm, st);
+  }
+  return cudaErrorInvalidValue;
+}
+// to_p != 0: FP64 -> prec, else prec -> FP64
+cudaError_t convert_any(int prec, int to_p, const VecArgs &v, int sm, cudaStream_t st) {
+  switch (prec) {
+    case P_F64: return convert_launch<P_F64>(to_p, v, sm, st);
+    case P_F32: return convert_launch<P_F32>(to_p, v, sm, st);
+    case P_F16: return convert_launch<P_F16>(to_p, v, sm, st);
+    case P_BF16: return convert_launch<P_BF16>(to_p, v, sm, st);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t accum_any(int prec, const VecArgs &v, int sm, cudaStream_t st) {
+  switch (prec) {
+    case P_F64: return accum_launch<P_F64>(v, sm, st);
+    case P_F32: return accum_launch<P_F32>(v, sm, st);
+    case P_F16: return accum_launch<P_F16>(v, sm, st);
+    case P_BF16: return accum_launch<P_BF16>(v, sm, st);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t pack_any(int prec, const double *host, Field f, Geom g, int par, int sm, cudaStream_t st) {
+  switch (prec) {
+    case P_F64: return pack_launch<P_F64>(host, f, g, par, sm, st);
+    case P_F32: return pack_launch<P_F32>(host, f, g, par, sm, st);
+    case P_F16: return pack_launch<P_F16>(host, f, g, par, sm, st);
+    case P_BF16: return pack_launch<P_BF16>(host, f, g, par, sm, st);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t unpack_any(int prec, Field f, double *host, Geom g, int par, int sm, cudaStream_t st) {
+  switch (prec) {
+    case P_F64: return unpack_launch<P_F64>(f, host, g, par, sm, st);
+    case P_F32: return unpack_launch<P_F32>(f, host, g, par, sm, st);
+    case P_F16: return unpack_launch<P_F16>(f, host, g, par, sm, st);
+    case P_BF16: return unpack_launch<P_BF16>(f, host, g, par, sm, st);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t gauge_any(int prec, const double *U, void *G, Geom g, int par, int sm, cudaStream_t st) {
+  switch (prec) {
+    case P_F64: return gauge_launch<P_F64>(U, G, g, par, sm, st);
+    case P_F32: return gauge_launch<P_F32>(U, G, g, par, sm, st);
+    case P_F16: return gauge_launch<P_F16>(U, G, g, par, sm, st);
+    case P_BF16: return gauge_launch<P_BF16>(U, G, g, par, sm, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+size_t link_bytes_per_site(int prec) {
+  return prec == P_F64 ? 8 * 18 * 8 : prec == P_F32 ? 8 * 18 * 4 : 8 * 12 * 2;
+}
+
+// doubled gauge field of precision prec, built on first use
+dwf_status ensure_gauge(dwf_ctx *c, int prec, cudaStream_t st) {
+  if (!c->gauge_loaded) return fail(c, DWF_ENOGAUGE, "dwf_load_gauge has not been called");
+  if (c->gauge_ready[prec]) return DWF_OK;
+  for (int p = 0; p < 2; ++p) {
+    if (!c->d_gauge[prec][p]) CK(cudaMalloc(&c->d_gauge[prec][p], (size_t)c->h * link_bytes_per_site(prec)));
+    Timed t(c, st, DWF_KC_OTHER);
+    CK(gauge_any(prec, c->d_U, c->d_gauge[prec][p], geom(c), p, c->sm_count, st));
+  }
+  c->gauge_ready[prec] = true;
+  return DWF_OK;
+}
+
+HopArgs hop_args(dwf_ctx *c, int prec, int outpar) {
+  HopArgs a;
+  memset(&a, 0, sizeof(a));
+  a.gauge = c->d_gauge[prec][outpar];
+  a.nbr = c->d_nbr[outpar];
+  a.h = c->h;
+  a.Ns = c->Ns;
+  a.fin = FIN_RED2;
+  a.sc = c->d_sc;
+  a.partials = c->d_part;
+  a.ticket = c->d_ticket;
+  return a;
+}
+
+dwf_status hop(dwf_ctx *c, cudaStream_t st, int prec, int epi, HopArgs a, int cls) {
+  Timed t(c, st, cls);
+  CK(hop_any(prec, epi, a, st));
+  return DWF_OK;
+}
+
+const void *dmat(dwf_ctx *c, int prec, int kind) { return c->dmat[mat_index(prec)][kind]; }
+
+dwf_status smix(dwf_ctx *c, cudaStream_t st, int prec, int mode, Field in, Field out, int kind,
+                double coef, int cls, Field out2 = Field{nullptr, nullptr}, int kind2 = MK_ID,
+                Field r = Field{nullptr, nullptr}, Field p = Field{nullptr, nullptr}, int use_flag = 0) {
+  SmixArgs a;
+  memset(&a, 0, sizeof(a));
+  a.in = in;
+  a.out = out;
+  a.out2 = out2;
+  a.r = r;
+  a.p = p;
+  a.K = dmat(c, prec, kind);
+  a.K2 = dmat(c, prec, kind2);
+  a.coef = coef;
+  a.h = c->h;
+  a.Ns = c->Ns;
+  a.use_flag = use_flag;
+  a.sc = c->d_sc;
+  Timed t(c, st, cls);
+  CK(smix_any(prec, mode, a, st));
+  return DWF_OK;
+}
+
+dwf_status norm2(dwf_ctx *c, cudaStream_t st, int prec, Field f, int fin) {
+  VecArgs v;
+  memset(&v, 0, sizeof(v));
+  v.a = f;
+  v.n = c->h * c->Ns;
+  v.Ns = c->Ns;
+  v.fin = fin;
+  v.sc = c->d_sc;
+  v.partials = c->d_part;
+  v.ticket = c->d_ticket;
+  Timed t(c, st, DWF_KC_OTHER);
+  CK(norm2_any(prec, v, c->sm_count, st));
+  return DWF_OK;
+}
+
+// dst (prec_dst) = src (prec_src); one side must be FP64 unless both are equal
+dwf_status convert(dwf_ctx *c, cudaStream_t st, int prec_src, Field src, int prec_dst, Field dst, int cls) {
+  VecArgs v;
+  memset(&v, 0, sizeof(v));
+  v.a = src;
+  v.b = dst;
+  v.n = c->h * c->Ns;
+  v.Ns = c->Ns;
+  Timed t(c, st, cls);
+  if (prec_src == P_F64) {
+    CK(convert_any(prec_dst, 1, v, c->sm_count, st));
+  } else if (prec_dst == P_F64) {
+    CK(convert_any(prec_src, 0, v, c->sm_count, st));
+  } else {
+    return fail(c, DWF_EINVAL, "conversion between two reduced precisions");
+  }
+  return DWF_OK;
+}
+
+dwf_status pull_scalars(dwf_ctx *c, cudaStream_t st) {
+  CK(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (c->h_sc->error) {
+    // a bounded wait gave up: clear the error word and the reduction ticket
+    cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), st);
+    c->h_sc->error = 0;
+    cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(CGScalars), cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+    return fail(c, DWF_ETIMEOUT, "a device-side wait for the TMA link copy timed out");
+  }
+  return DWF_OK;
+}
+
+dwf_status push_scalars(dwf_ctx *c, cudaStream_t st) {
+  CK(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(CGScalars), cudaMemcpyHostToDevice, st));
+  return DWF_OK;
+}
+
+// ------------------------------------------------------------------ operator compositions
+
+// q = C^dag v on Schur parity sp (Eq. 11, adjoint via gamma5-hermiticity of D_w):
+// C^dag v = g5 (1 - D^{sp,op} M5^T D^{op,sp} M5^T) g5 v
+//   w = M5^T g5 v;  t = M5^T D^{op,sp} w = -1/2 M5^T H w;  q = v + 1/2 g5 H t
+dwf_status op_cdag(dwf_ctx *c, cudaStream_t st, int prec, int sp, Field v, Field q, Field w, Field t,
+                   int cls) {
+  const int op = 1 - sp;
+  TRY(smix(c, st, prec, S_G5, v, w, MK_M5T, 1.0, cls));
+  HopArgs a = hop_args(c, prec, op);
+  a.in = w;
+  a.out = t;
+  a.K = dmat(c, prec, MK_M5T);
+  a.coef = -0.5;
+  TRY(hop(c, st, prec, E_M, a, cls));
+  HopArgs b = hop_args(c, prec, sp);
+  b.in = t;
+  b.y = v;
+  b.out = q;
+  b.coef = 0.5;
+  TRY(hop(c, st, prec, E_XPAY_G5, b, cls));
+  return DWF_OK;
+}
+
+// out = C v = v - M5 D^{sp,op} M5 D^{op,sp} v:  u = -1/2 M5 H v;  out = v + 1/2 M5 H u
+dwf_status op_c(dwf_ctx *c, cudaStream_t st, int prec, int sp, Field v, Field out, Field u, int cls) {
+  const int op = 1 - sp;
+  HopArgs a = hop_args(c, prec, op);
+  a.in = v;
+  a.out = u;
+  a.K = dmat(c, prec, MK_M5);
+  a.coef = -0.5;
+  TRY(hop(c, st, prec, E_M, a, cls));
+  HopArgs b = hop_args(c, prec, sp);
+  b.in = u;
+  b.y = v;
+  b.out = out;
+  b.K = dmat(c, prec, MK_M5);
+  b.coef = 0.5;
+  TRY(hop(c, st, prec, E_M_XPAY, b, cls));
+  return DWF_OK;
+}
+
+// full-lattice operator on both parities: out_p = Z in_p - 1/2 H (W in)_{1-p}
+// (kindW, kindZ) = (MK_W, MK_Z) gives D(mq) of Eq. 5; (MK_ID, MK_MASS) gives D_w of Eq. 2.
+dwf_status op_full(dwf_ctx *c, cudaStream_t st, int prec, const Field in[2], Field out[2], int kindW,
+                   int kindZ, int cls) {
+  Field t[2], z[2];
+  for (int p = 0; p < 2; ++p) {
+    TRY(get_buf(c, "full_t" + std::to_string(p), prec, &t[p]));
+    TRY(get_buf(c, "full_z" + std::to_string(p), prec, &z[p]));
+    TRY(smix(c, st, prec, S_DUAL, in[p], t[p], kindW, 1.0, cls, z[p], kindZ));
+  }
+  for (int p = 0; p < 2; ++p) {
+    HopArgs a = hop_args(c, prec, p);
+    a.in = t[1 - p];
+    a.y = z[p];
+    a.out = out[p];
+    a.coef = -0.5;
+    TRY(hop(c, st, prec, E_XPAY, a, cls));
+  }
+  return DWF_OK;
+}
+
+dwf_status check_ctx(dwf_ctx *c) {
+  if (!c) return DWF_EINVAL;
+  c->err.clear();
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return fail(c, DWF_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  return DWF_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+void begin_profile(dwf_ctx *c, bool on) {
+  c->profiling = on;
+  c->ev_used = 0;
+  c->prof.clear();
+}
+
+void end_profile(dwf_ctx *c, dwf_solve_stats *stats) {
+  if (!c->profiling) return;
+  if (stats)
+    for (auto &r : c->prof) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      stats->class_ms[r.cls] += ms;
+      stats->class_launches[r.cls] += 1;
+    }
+  c->profiling = false;
+}
+
+}  // namespace
+
+// ====================================================================== C-ABI
+
+extern "C" {
+
+const char *dwf_status_string(dwf_status st) { return status_name(st); }
+
+const char *dwf_last_error(const dwf_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+void dwf_solve_params_default(dwf_solve_params *p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->tol = 1e-10;
+  p->delta = 0.0;
+  p->max_iter = 100000;
+  p->inner_prec = DWF_PREC_F32;
+  p->mode = DWF_MODE_AUTO;
+  p->system = DWF_SYS_FULL;
+  p->schur_parity = 1;
+  p->check_every = 8;
+  p->use_graph = 1;
+  p->profile = 0;
+}
+
+dwf_status dwf_create(const int dims[4], int Ns, double m0, double mq, const double *omega,
+                      const double *sigma, dwf_ctx **out) {
+  if (!dims || !omega || !sigma || !out) return DWF_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < 4; ++i)
+    if (dims[i] < 2 || (dims[i] & 1)) return DWF_EINVAL;
+  if (Ns < 1 || Ns > 64 || !(m0 > 0.0 && m0 < 2.0) || !(mq >= 0.0)) return DWF_EINVAL;
+  for (int s = 0; s < Ns; ++s)
+    if (!(omega[s] > 0.0) || !std::isfinite(sigma[s])) return DWF_EINVAL;
+  const long V4 = (long)dims[0] * dims[1] * dims[2] * dims[3];
+  if (V4 / 2 > (1L << 30)) return DWF_EINVAL;
+
+  dwf_ctx *c = new dwf_ctx();
+  for (int i = 0; i < 4; ++i) c->dims[i] = dims[i];
+  c->Ns = Ns;
+  c->V4 = V4;
+  c->h = V4 / 2;
+  c->m0 = m0;
+  c->mq = mq;
+  c->omega.assign(omega, omega + Ns);
+  c->sigma.assign(sigma, sigma + Ns);
+  if (!build_matrices(c)) {
+    delete c;
+    return DWF_EINVAL;
+  }
+  auto bail = [&](cudaError_t e) {
+    dwf_destroy(c);
+    return e == cudaErrorMemoryAllocation ? DWF_ENOMEM : DWF_ECUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaGetDevice(&c->device)) != cudaSuccess) return bail(e);
+  if ((e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess)
+    return bail(e);
+  if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(e);
+  // matrices in both arithmetic precisions, kernel order K[chi][t][s]
+  const size_t nm = (size_t)2 * Ns * Ns;
+  std::vector<double> kd(nm);
+  std::vector<float> kf(nm);
+  for (int k = 0; k < MK_COUNT; ++k) {
+    for (int chi = 0; chi < 2; ++chi)
+      for (int s = 0; s < Ns; ++s)
+        for (int t = 0; t < Ns; ++t) {
+          const double v = c->mat[k][(size_t)chi * Ns * Ns + (size_t)s * Ns + t];
+          kd[(size_t)chi * Ns * Ns + (size_t)t * Ns + s] = v;
+          kf[(size_t)chi * Ns * Ns + (size_t)t * Ns + s] = (float)v;
+        }
+    if ((e = cudaMalloc(&c->dmat[0][k], nm * sizeof(double))) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&c->dmat[1][k], nm * sizeof(float))) != cudaSuccess) return bail(e);
+    if ((e = cudaMemcpy(c->dmat[0][k], kd.data(), nm * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(e);
+    if ((e = cudaMemcpy(c->dmat[1][k], kf.data(), nm * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(e);
+  }
+  Geom g = geom(c);
+  for (int p = 0; p < 2; ++p) {
+    if ((e = cudaMalloc((void **)&c->d_nbr[p], (size_t)c->h * 8 * sizeof(int))) != cudaSuccess) return bail(e);
+    if ((e = neighbours_launch(c->d_nbr[p], g, p, c->sm_count, c->stream)) != cudaSuccess) return bail(e);
+  }
+  if ((e = cudaMalloc((void **)&c->d_sc, sizeof(CGScalars))) != cudaSuccess) return bail(e);
+  if ((e = cudaMallocHost((void **)&c->h_sc, sizeof(CGScalars))) != cudaSuccess) return bail(e);
+  memset(c->h_sc, 0, sizeof(CGScalars));
+  c->part_len = std::max<size_t>((size_t)c->h, 8192);
+  if ((e = cudaMalloc((void **)&c->d_part, c->part_len * sizeof(double))) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc((void **)&c->d_ticket, sizeof(unsigned))) != cudaSuccess) return bail(e);
+  if ((e = cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream)) != cudaSuccess) return bail(e);
+  if ((e = cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(CGScalars), cudaMemcpyHostToDevice, c->stream)) !=
+      cudaSuccess)
+    return bail(e);
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(e);
+  *out = c;
+  return DWF_OK;
+}
+
+dwf_status dwf_destroy(dwf_ctx *c) {
+  if (!c) return DWF_OK;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto &kv : c->bufs) {
+    if (kv.second.v) cudaFree(kv.second.v);
+    if (kv.second.nrm) cudaFree(kv.second.nrm);
+  }
+  for (auto &row : c->dmat)
+    for (void *p : row)
+      if (p) cudaFree(p);
+  for (auto &row : c->d_gauge)
+    for (void *p : row)
+      if (p) cudaFree(p);
+  for (int *p : c->d_nbr)
+    if (p) cudaFree(p);
+  if (c->d_U) cudaFree(c->d_U);
+  if (c->d_sc) cudaFree(c->d_sc);
+  if (c->h_sc) cudaFreeHost(c->h_sc);
+  if (c->d_part) cudaFree(c->d_part);
+  if (c->d_ticket) cudaFree(c->d_ticket);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return DWF_OK;
+}
+
+dwf_status dwf_load_gauge_dev(dwf_ctx *c, const double *d_U, void *stream) {
+  TRY(check_ctx(c));
+  if (!d_U) return fail(c, DWF_EINVAL, "null gauge pointer");
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  const size_t bytes = (size_t)c->V4 * 72 * sizeof(double);
+  if (!c->d_U) CK(cudaMalloc((void **)&c->d_U, bytes));
+  CK(cudaMemcpyAsync(c->d_U, d_U, bytes, cudaMemcpyDeviceToDevice, st));
+  c->gauge_loaded = true;
+  for (int p = 0; p < 4; ++p) c->gauge_ready[p] = false;
+  // the FP64 and FP32 forms are always needed (restart operator, inner CG)
+  TRY(ensure_gauge(c, P_F64, st));
+  TRY(ensure_gauge(c, P_F32, st));
+  CK(cudaStreamSynchronize(st));
+  return DWF_OK;
+}
+
+dwf_status dwf_load_gauge(dwf_ctx *c, const double *U) {
+  TRY(check_ctx(c));
+  if (!U) return fail(c, DWF_EINVAL, "null gauge pointer");
+  const size_t bytes = (size_t)c->V4 * 72 * sizeof(double);
+  if (!c->d_U) CK(cudaMalloc((void **)&c->d_U, bytes));
+  CK(cudaMemcpyAsync(c->d_U, U, bytes, cudaMemcpyHostToDevice, c->stream));
+  c->gauge_loaded = true;
+  for (int p = 0; p < 4; ++p) c->gauge_ready[p] = false;
+  TRY(ensure_gauge(c, P_F64, c->stream));
+  TRY(ensure_gauge(c, P_F32, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return DWF_OK;
+}
+
+dwf_status dwf_apply_eo_dev(dwf_ctx *c, int op, int prec, int parity, const double *d_in, double *d_out,
+                            void *stream) {
+  TRY(check_ctx(c));
+  if (!d_in || !d_out || !aligned16(d_in) || !aligned16(d_out))
+    return fail(c, DWF_EINVAL, "null or non-16-byte-aligned field pointer");
+  if (!valid_prec(prec)) return fail(c, DWF_EINVAL, "unknown precision");
+  if (op < DWF_OP_DEO || op > DWF_OP_DW) return fail(c, DWF_EINVAL, "unknown operator");
+  const bool needs_parity = op >= DWF_OP_M5 && op <= DWF_OP_CCDAG;
+  if (needs_parity && parity != 0 && parity != 1) return fail(c, DWF_EINVAL, "parity must be 0 or 1");
+  const size_t full = (size_t)c->V4 * c->Ns * 24 * sizeof(double);
+  if ((const char *)d_in < (const char *)d_out + full && (const char *)d_out < (const char *)d_in + full)
+    return fail(c, DWF_EINVAL, "in and out overlap");
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  TRY(ensure_gauge(c, prec, st));
+  const Geom g = geom(c);
+  const int cls = DWF_KC_OTHER;
+  CK(cudaMemsetAsync(d_out, 0, full, st));
+
+  Field in[2], out[2], tA, tB, tC;
+  for (int p = 0; p < 2; ++p) {
+    TRY(get_buf(c, "ap_in" + std::to_string(p), prec, &in[p]));
+    TRY(get_buf(c, "ap_out" + std::to_string(p), prec, &out[p]));
+  }
+  TRY(get_buf(c, "ap_tA", prec, &tA));
+  TRY(get_buf(c, "ap_tB", prec, &tB));
+  TRY(get_buf(c, "ap_tC", prec, &tC));
+  auto pack = [&](int p) -> dwf_status {
+    Timed t(c, st, cls);
+    CK(pack_any(prec, d_in, in[p], g, p, c->sm_count, st));
+    return DWF_OK;
+  };
+  auto unpack = [&](int p) -> dwf_status {
+    Timed t(c, st, cls);
+    CK(unpack_any(prec, out[p], d_out, g, p, c->sm_count, st));
+    return DWF_OK;
+  };
+  switch (op) {
+    case DWF_OP_DEO:
+    case DWF_OP_DOE: {
+      const int outp = op == DWF_OP_DEO ? 0 : 1;
+      TRY(pack(1 - outp));
+      HopArgs a = hop_args(c, prec, outp);
+      a.in = in[1 - outp];
+      a.out = out[outp];
+      a.coef = -0.5;
+      TRY(hop(c, st, prec, E_PLAIN, a, cls));
+      TRY(unpack(outp));
+      break;
+    }
+    case DWF_OP_M5:
+    case DWF_OP_M5T:
+      TRY(pack(parity));
+      TRY(smix(c, st, prec, S_PLAIN, in[parity], out[parity], op == DWF_OP_M5 ? MK_M5 : MK_M5T, 1.0, cls));
+      TRY(unpack(parity));
+      break;
+    case DWF_OP_C:
+      TRY(pack(parity));
+      TRY(op_c(c, st, prec, parity, in[parity], out[parity], tA, cls));
+      TRY(unpack(parity));
+      break;
+    case DWF_OP_CDAG:
+      TRY(pack(parity));
+      TRY(op_cdag(c, st, prec, parity, in[parity], out[parity], tA, tB, cls));
+      TRY(unpack(parity));
+      break;
+    case DWF_OP_CCDAG:
+      TRY(pack(parity));
+      TRY(op_cdag(c, st, prec, parity, in[parity], tC, tA, tB, cls));
+      TRY(op_c(c, st, prec, parity, tC, out[parity], tA, cls));
+      TRY(unpack(parity));
+      break;
+    case DWF_OP_DFULL:
+    case DWF_OP_DW:
+      TRY(pack(0));
+      TRY(pack(1));
+      TRY(op_full(c, st, prec, in, out, op == DWF_OP_DFULL ? MK_W : MK_ID, op == DWF_OP_DFULL ? MK_Z : MK_MASS,
+                  cls));
+      TRY(unpack(0));
+      TRY(unpack(1));
+      break;
+  }
+  CK(cudaStreamSynchronize(st));
+  return pull_scalars(c, st);
+}
+
+dwf_status dwf_apply_eo(dwf_ctx *c, int op, int prec, int parity, const double *in, double *out) {
+  TRY(check_ctx(c));
+  if (!in || !out) return fail(c, DWF_EINVAL, "null field pointer");
+  const size_t full = (size_t)c->V4 * c->Ns * 24 * sizeof(double);
+  void *din, *dout;
+  TRY(get_raw(c, "host_in", full, &din));
+  TRY(get_raw(c, "host_out", full, &dout));
+  CK(cudaMemcpyAsync(din, in, full, cudaMemcpyHostToDevice, c->stream));
+  TRY(dwf_apply_eo_dev(c, op, prec, parity, (const double *)din, (double *)dout, c->stream));
+  CK(cudaMemcpyAsync(out, dout, full, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return DWF_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== solver
+
+namespace {
+
+struct SolveState {
+  int prec, sp, op;
+  Field b, xh, rh, w64, t64, q64, u64;  // FP64, Schur parity (t64, u64: other parity)
+  Field x, r, p, q, w, t, u;            // inner precision
+};
+
+// one inner CG iteration on A = C C^dag (Algorithm 1), five kernels:
+//   p = r + beta p, w = M5^T g5 p | t = -1/2 M5^T H w | q = p + 1/2 g5 H t, |q|^2
+//   u = -1/2 M5 H q | Ap = q + 1/2 M5 H u, r -= alpha Ap, x += alpha p, |r|^2, beta
+dwf_status cg_iteration(dwf_ctx *c, cudaStream_t st, const SolveState &S) {
+  const int P = S.prec;
+  TRY(smix(c, st, P, S_CGP, Field{nullptr, nullptr}, S.w, MK_M5T, 1.0, DWF_KC_SMIX_P, Field{nullptr, nullptr},
+           MK_ID, S.r, S.p, 1));
+  HopArgs a = hop_args(c, P, S.op);
+  a.in = S.w;
+  a.out = S.t;
+  a.K = dmat(c, P, MK_M5T);
+  a.coef = -0.5;
+  a.use_flag = 1;
+  TRY(hop(c, st, P, E_M, a, DWF_KC_HOP_M5));
+  HopArgs b = hop_args(c, P, S.sp);
+  b.in = S.t;
+  b.y = S.p;
+  b.out = S.q;
+  b.coef = 0.5;
+  b.fin = FIN_QQ;
+  b.use_flag = 1;
+  TRY(hop(c, st, P, E_XPAY_G5, b, DWF_KC_HOP_XPAY));
+  HopArgs d = hop_args(c, P, S.op);
+  d.in = S.q;
+  d.out = S.u;
+  d.K = dmat(c, P, MK_M5);
+  d.coef = -0.5;
+  d.use_flag = 1;
+  TRY(hop(c, st, P, E_M, d, DWF_KC_HOP_M5));
+  HopArgs e = hop_args(c, P, S.sp);
+  e.in = S.u;
+  e.y = S.q;
+  e.r = S.r;
+  e.x = S.x;
+  e.p = S.p;
+  e.K = dmat(c, P, MK_M5);
+  e.coef = 0.5;
+  e.fin = FIN_CG;
+  e.use_flag = 1;
+  TRY(hop(c, st, P, E_CG_UPDATE, e, DWF_KC_HOP_UPDATE));
+  return DWF_OK;
+}
+
+// FP64 restart (Algorithm 2): x_hat += x, x = 0, r_hat = b - C C^dag x_hat, |r_hat|^2 -> red,
+// r = r_hat in the inner precision, |r|^2 -> red2
+dwf_status fp64_restart(dwf_ctx *c, cudaStream_t st, const SolveState &S) {
+  {
+    VecArgs v;
+    memset(&v, 0, sizeof(v));
+    v.a = S.xh;
+    v.b = S.x;
+    v.n = c->h * c->Ns;
+    v.Ns = c->Ns;
+    Timed t(c, st, DWF_KC_F64);
+    CK(accum_any(S.prec, v, c->sm_count, st));
+  }
+  TRY(smix(c, st, P_F64, S_G5, S.xh, S.w64, MK_M5T, 1.0, DWF_KC_F64));
+  HopArgs a = hop_args(c, P_F64, S.op);
+  a.in = S.w64;
+  a.out = S.t64;
+  a.K = dmat(c, P_F64, MK_M5T);
+  a.coef = -0.5;
+  TRY(hop(c, st, P_F64, E_M, a, DWF_KC_F64));
+  HopArgs b = hop_args(c, P_F64, S.sp);
+  b.in = S.t64;
+  b.y = S.xh;
+  b.out = S.q64;
+  b.coef = 0.5;
+  b.fin = FIN_NONE;
+  TRY(hop(c, st, P_F64, E_XPAY_G5, b, DWF_KC_F64));
+  HopArgs d = hop_args(c, P_F64, S.op);
+  d.in = S.q64;
+  d.out = S.u64;
+  d.K = dmat(c, P_F64, MK_M5);
+  d.coef = -0.5;
+  TRY(hop(c, st, P_F64, E_M, d, DWF_KC_F64));
+  HopArgs e = hop_args(c, P_F64, S.sp);
+  e.in = S.u64;
+  e.y = S.q64;
+  e.b = S.b;
+  e.out = S.rh;
+  e.K = dmat(c, P_F64, MK_M5);
+  e.coef = 0.5;
+  e.fin = FIN_RED;
+  TRY(hop(c, st, P_F64, E_RESID, e, DWF_KC_F64));
+  TRY(convert(c, st, P_F64, S.rh, S.prec, S.r, DWF_KC_F64));
+  TRY(norm2(c, st, S.prec, S.r, FIN_RED2));
+  return DWF_OK;
+}
+
+// counted flops per 5D half-site (fixed convention; hop 1320, dense M5 24 (2 Ns - 1))
+double flops_cg_iter(int Ns) { return 5472.0 + 192.0 * Ns; }
+double flops_restart(int Ns) { return 5328.0 + 192.0 * Ns; }
+double flops_prep_recon(int Ns) { return 5160.0 + 384.0 * Ns; }
+
+}  // namespace
+
+extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_sol, const dwf_solve_params *pp,
+                                    dwf_solve_stats *stats, void *stream) {
+  TRY(check_ctx(c));
+  dwf_solve_params prm;
+  if (pp) prm = *pp;
+  else dwf_solve_params_default(&prm);
+  if (!d_rhs || !d_sol || !aligned16(d_rhs) || !aligned16(d_sol))
+    return fail(c, DWF_EINVAL, "null or non-16-byte-aligned field pointer");
+  if (!valid_prec(prm.inner_prec)) return fail(c, DWF_EINVAL, "unknown inner precision");
+  if (prm.system != DWF_SYS_FULL && prm.system != DWF_SYS_NORMAL) return fail(c, DWF_EINVAL, "unknown system");
+  if (prm.schur_parity != 0 && prm.schur_parity != 1) return fail(c, DWF_EINVAL, "schur_parity must be 0 or 1");
+  if (prm.mode < DWF_MODE_AUTO || prm.mode > DWF_MODE_DEFECT) return fail(c, DWF_EINVAL, "unknown mode");
+  if (!(prm.tol > 0.0) || prm.max_iter < 1) return fail(c, DWF_EINVAL, "tol must be > 0 and max_iter >= 1");
+  if (prm.check_every < 1) prm.check_every = 8;
+  const double delta = prm.delta > 0.0 ? prm.delta : (prm.inner_prec >= DWF_PREC_F16 ? 0.3 : 0.1);
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  dwf_solve_stats local;
+  dwf_solve_stats *S_out = stats ? stats : &local;
+  memset(S_out, 0, sizeof(*S_out));
+  begin_profile(c, prm.profile != 0);
+  const long long launches0 = c->launches;
+  TRY(ensure_gauge(c, P_F64, st));
+  TRY(ensure_gauge(c, prm.inner_prec, st));
+
+  cudaEvent_t ev0 = next_event(c), ev1 = next_event(c);
+  CK(cudaEventRecord(ev0, st));
+
+  SolveState S;
+  S.prec = prm.inner_prec;
+  S.sp = prm.schur_parity;
+  S.op = 1 - S.sp;
+  TRY(get_buf(c, "b", P_F64, &S.b));
+  TRY(get_buf(c, "xh", P_F64, &S.xh));
+  TRY(get_buf(c, "rh", P_F64, &S.rh));
+  TRY(get_buf(c, "w64", P_F64, &S.w64));
+  TRY(get_buf(c, "t64", P_F64, &S.t64));
+  TRY(get_buf(c, "q64", P_F64, &S.q64));
+  TRY(get_buf(c, "u64", P_F64, &S.u64));
+  TRY(get_buf(c, "cg_x", S.prec, &S.x));
+  TRY(get_buf(c, "cg_r", S.prec, &S.r));
+  TRY(get_buf(c, "cg_p", S.prec, &S.p));
+  TRY(get_buf(c, "cg_q", S.prec, &S.q));
+  TRY(get_buf(c, "cg_w", S.prec, &S.w));
+  TRY(get_buf(c, "cg_t", S.prec, &S.t));
+  TRY(get_buf(c, "cg_u", S.prec, &S.u));
+  const Geom g = geom(c);
+  const bool full = prm.system == DWF_SYS_FULL;
+  Field eta[2], etap[2];
+  const size_t nbytes64 = (size_t)c->h * c->Ns * 192;
+
+  // ---- source: b on the Schur parity (Eq. 10 for the full system)
+  if (full) {
+    for (int p = 0; p < 2; ++p) {
+      TRY(get_buf(c, "eta" + std::to_string(p), P_F64, &eta[p]));
+      TRY(get_buf(c, "etap" + std::to_string(p), P_F64, &etap[p]));
+      {
+        Timed t(c, st, DWF_KC_F64);
+        CK(pack_any(P_F64, d_rhs, eta[p], g, p, c->sm_count, st));
+      }
+      // eta' = S1 eta
+      TRY(smix(c, st, P_F64, S_PLAIN, eta[p], etap[p], MK_S1, 1.0, DWF_KC_F64));
+    }
+    // b = eta'_sp - M5 D^{sp,op} eta'_op = eta'_sp + 1/2 M5 H eta'_op
+    HopArgs a = hop_args(c, P_F64, S.sp);
+    a.in = etap[S.op];
+    a.y = etap[S.sp];
+    a.out = S.b;
+    a.K = dmat(c, P_F64, MK_M5);
+    a.coef = 0.5;
+    TRY(hop(c, st, P_F64, E_M_XPAY, a, DWF_KC_F64));
+  } else {
+    Timed t(c, st, DWF_KC_F64);
+    CK(pack_any(P_F64, d_rhs, S.b, g, S.sp, c->sm_count, st));
+  }
+  TRY(norm2(c, st, P_F64, S.b, FIN_RED));
+  // x_hat = 0, r_hat = b, r = b (inner precision), x = 0, p = 0
+  CK(cudaMemsetAsync(S.xh.v, 0, nbytes64, st));
+  CK(cudaMemcpyAsync(S.rh.v, S.b.v, nbytes64, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(S.x.v, 0, (size_t)c->h * c->Ns * site_bytes(S.prec), st));
+  CK(cudaMemsetAsync(S.p.v, 0, (size_t)c->h * c->Ns * site_bytes(S.prec), st));
+  if (S.x.nrm) {
+    CK(cudaMemsetAsync(S.x.nrm, 0, (size_t)c->h * c->Ns * sizeof(float), st));
+    CK(cudaMemsetAsync(S.p.nrm, 0, (size_t)c->h * c->Ns * sizeof(float), st));
+  }
+  TRY(convert(c, st, P_F64, S.b, S.prec, S.r, DWF_KC_OTHER));
+  TRY(norm2(c, st, S.prec, S.r, FIN_RED2));
+  TRY(pull_scalars(c, st));
+  const double bnorm2 = c->h_sc->red;
+  const double tol2 = prm.tol * prm.tol;
+
+  int iters = 0, restarts = 0, mode_now = prm.mode == DWF_MODE_DEFECT ? DWF_MODE_DEFECT : DWF_MODE_RELIABLE;
+  double rhat2 = bnorm2, prev_rhat2 = bnorm2;
+  bool converged = bnorm2 == 0.0;
+  dwf_status result = DWF_OK;
+  // (re)arm the inner CG after a restart: r already holds r_hat in the inner precision and
+  // red2 = |r|^2.  Reliable updates keep p (beta from the recomputed residual), defect
+  // correction restarts from p = r (beta = 0).
+  auto arm = [&](double tol_now, bool first) -> dwf_status {
+    CGScalars &h = *c->h_sc;
+    const double rr_conv = h.red2;
+    if (first) {
+      h.rr_old = rr_conv;
+      h.qq = 1.0;
+      h.beta = 0.0;
+      h.iter = 0;
+      h.iter_cap = prm.max_iter;
+      h.error = 0;
+      h.delta2 = delta * delta;
+    } else {
+      h.beta = (mode_now == DWF_MODE_DEFECT) ? 0.0 : rr_conv / h.rr_old;
+    }
+    h.rr = rr_conv;
+    h.rmax2 = rr_conv;
+    h.target2 = tol_now * tol_now * bnorm2;
+    h.restart_flag = 0;
+    return push_scalars(c, st);
+  };
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  struct GraphGuard {
+    cudaGraphExec_t &e;
+    cudaGraph_t &g;
+    ~GraphGuard() {
+      if (e) cudaGraphExecDestroy(e);
+      if (g) cudaGraphDestroy(g);
+    }
+  } graph_guard{gexec, graph};
+  const bool use_graph = prm.use_graph && !c->profiling;
+  bool first_batch = true;
+  // mixed-precision CG until |b - A x_hat| <= tol_now |b| (FP64)
+  auto cg_loop = [&](double tol_now) -> dwf_status {
+    const double tol2 = tol_now * tol_now;
+    converged = rhat2 <= tol2 * bnorm2;
+    while (!converged) {
+      // ---- one batch of inner iterations (the device skips the rest once a restart is due)
+      if (use_graph && !first_batch) {
+        if (!gexec) {
+          CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+          const long long l0 = c->launches;
+          for (int k = 0; k < prm.check_every; ++k) {
+            dwf_status s2 = cg_iteration(c, st, S);
+            if (s2 != DWF_OK) {
+              cudaStreamEndCapture(st, &graph);
+              return s2;
+            }
+          }
+          c->launches = l0;
+          CK(cudaStreamEndCapture(st, &graph));
+          CK(cudaGraphInstantiate(&gexec, graph, 0));
+        }
+        CK(cudaGraphLaunch(gexec, st));
+        c->launches += 5LL * prm.check_every;
+      } else {
+        for (int k = 0; k < prm.check_every; ++k) TRY(cg_iteration(c, st, S));
+      }
+      first_batch = false;
+      TRY(pull_scalars(c, st));
+      if (!c->h_sc->restart_flag) continue;
+      iters = c->h_sc->iter;
+      // ---- reliable update / defect correction restart in FP64
+      TRY(fp64_restart(c, st, S));
+      TRY(pull_scalars(c, st));
+      ++restarts;
+      rhat2 = c->h_sc->red;
+      if (!std::isfinite(rhat2)) return fail(c, DWF_ENOCONV, "residual is not finite");
+      if (rhat2 <= tol2 * bnorm2) {
+        converged = true;
+        break;
+      }
+      if (iters >= prm.max_iter) return fail(c, DWF_ENOCONV, "max_iter reached");
+      // Sec. 2.3: fall back to defect correction when the reliable updates stop converging
+      if (prm.mode == DWF_MODE_AUTO && mode_now == DWF_MODE_RELIABLE && rhat2 > prev_rhat2)
+        mode_now = DWF_MODE_DEFECT;
+      prev_rhat2 = rhat2;
+      TRY(arm(tol_now, false));
+    }
+    return DWF_OK;
+  };
+  // phi_sp = C^dag x_hat;  phi_op = eta'_op - M5 D^{op,sp} phi_sp;  psi = S2 phi, unpacked to
+  // d_sol; then |eta - D psi| / |eta| in FP64
+  auto reconstruct = [&](double *res_full) -> dwf_status {
+    Field phi[2], psi[2], dpsi[2];
+    for (int p = 0; p < 2; ++p) {
+      TRY(get_buf(c, "phi" + std::to_string(p), P_F64, &phi[p]));
+      TRY(get_buf(c, "psi" + std::to_string(p), P_F64, &psi[p]));
+      TRY(get_buf(c, "dpsi" + std::to_string(p), P_F64, &dpsi[p]));
+    }
+    TRY(op_cdag(c, st, P_F64, S.sp, S.xh, phi[S.sp], S.w64, S.t64, DWF_KC_F64));
+    HopArgs a = hop_args(c, P_F64, S.op);
+    a.in = phi[S.sp];
+    a.y = etap[S.op];
+    a.out = phi[S.op];
+    a.K = dmat(c, P_F64, MK_M5);
+    a.coef = 0.5;
+    TRY(hop(c, st, P_F64, E_M_XPAY, a, DWF_KC_F64));
+    for (int p = 0; p < 2; ++p) {
+      TRY(smix(c, st, P_F64, S_PLAIN, phi[p], psi[p], MK_S2, 1.0, DWF_KC_F64));
+      Timed t(c, st, DWF_KC_F64);
+      CK(unpack_any(P_F64, psi[p], d_sol, g, p, c->sm_count, st));
+    }
+    TRY(op_full(c, st, P_F64, psi, dpsi, MK_W, MK_Z, DWF_KC_F64));
+    double num = 0, den = 0;
+    for (int p = 0; p < 2; ++p) {
+      VecArgs v;
+      memset(&v, 0, sizeof(v));
+      v.a = eta[p];
+      v.b = dpsi[p];
+      v.n = c->h * c->Ns;
+      v.Ns = c->Ns;
+      v.fin = FIN_RED;
+      v.sc = c->d_sc;
+      v.partials = c->d_part;
+      v.ticket = c->d_ticket;
+      {
+        Timed t(c, st, DWF_KC_F64);
+        CK(diff_norm2_launch(v, c->sm_count, st));
+      }
+      TRY(norm2(c, st, P_F64, eta[p], FIN_RED2));
+      TRY(pull_scalars(c, st));
+      num += c->h_sc->red;
+      den += c->h_sc->red2;
+    }
+    *res_full = den > 0 ? sqrt(num / den) : 0.0;
+    return DWF_OK;
+  };
+
+  TRY(arm(prm.tol, true));
+  result = cg_loop(prm.tol);
+  if (result == DWF_OK && full) {
+    double res_full = 0;
+    TRY(reconstruct(&res_full));
+    // the full-system residual exceeds the Schur one by at most cond(S1); if it misses
+    // the target, tighten the Schur tolerance once and continue from x_hat
+    if (res_full > prm.tol && converged) {
+      const double tighter = prm.tol * std::min(0.1, 0.5 * prm.tol / res_full);
+      TRY(arm(tighter, false));
+      result = cg_loop(tighter);
+      if (result == DWF_OK) TRY(reconstruct(&res_full));
+    }
+    S_out->true_res_full = res_full;
+  } else if (result == DWF_OK || result == DWF_ENOCONV) {
+    if (full) {
+      double res_full = 0;
+      TRY(reconstruct(&res_full));
+      S_out->true_res_full = res_full;
+    } else {
+      CK(cudaMemsetAsync(d_sol, 0, (size_t)c->V4 * c->Ns * 24 * sizeof(double), st));
+      Timed t(c, st, DWF_KC_F64);
+      CK(unpack_any(P_F64, S.xh, d_sol, g, S.sp, c->sm_count, st));
+    }
+  }
+  iters = c->h_sc->iter;
+  CK(cudaEventRecord(ev1, st));
+  CK(cudaStreamSynchronize(st));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  S_out->iters = iters;
+  S_out->restarts = restarts;
+  S_out->mode_used = mode_now;
+  S_out->converged = converged ? 1 : 0;
+  S_out->true_res = bnorm2 > 0 ? sqrt(rhat2 / bnorm2) : 0.0;
+  const double n = (double)c->h * c->Ns;
+  S_out->flops = n * (iters * flops_cg_iter(c->Ns) + restarts * flops_restart(c->Ns) +
+                      (full ? flops_prep_recon(c->Ns) : 0.0));
+  S_out->time_ms = ms;
+  S_out->bytes_hop_m5 = n * (2.0 * site_bytes(S.prec) + 8.0 * link_bytes_per_site(S.prec) / 8.0 / c->Ns);
+  end_profile(c, S_out);
+  S_out->kernel_launches = c->launches - launches0;
+  if (result == DWF_OK && !converged) result = fail(c, DWF_ENOCONV, "not converged");
+  return result;
+}
+
+extern "C" dwf_status dwf_solve(dwf_ctx *c, const double *rhs, double *sol, const dwf_solve_params *pp,
+                                dwf_solve_stats *stats) {
+  TRY(check_ctx(c));
+  if (!rhs || !sol) return fail(c, DWF_EINVAL, "null field pointer");
+  const size_t full = (size_t)c->V4 * c->Ns * 24 * sizeof(double);
+  void *din, *dout;
+  TRY(get_raw(c, "host_in", full, &din));
+  TRY(get_raw(c, "host_out", full, &dout));
+  CK(cudaMemcpyAsync(din, rhs, full, cudaMemcpyHostToDevice, c->stream));
+  dwf_status s = dwf_solve_dev(c, (const double *)din, (double *)dout, pp, stats, c->stream);
+  if (s != DWF_OK && s != DWF_ENOCONV) return s;
+  CK(cudaMemcpyAsync(sol, dout, full, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return s;
+}

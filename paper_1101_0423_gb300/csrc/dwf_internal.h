@@ -1,0 +1,63 @@
+// dwf_internal.h -- host-side state of a dwf_ctx (library-internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/dwf.h"
+#include "dwf_launch.cuh"
+
+namespace dwf {
+
+// matrices along s held per context (kernel order K[chi][t][s] on the device)
+enum MatKind { MK_M5 = 0, MK_M5T, MK_S1, MK_S2, MK_W, MK_Z, MK_ID, MK_MASS, MK_COUNT };
+
+struct Buf {
+  void *v = nullptr;
+  float *nrm = nullptr;
+  size_t bytes = 0;
+};
+
+// one profiled launch: kernel class and its event pair
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+}  // namespace dwf
+
+struct dwf_ctx {
+  int dims[4];
+  int Ns;
+  long V4, h;
+  double m0, mq;
+  std::vector<double> omega, sigma;
+  // host FP64 matrices, row-major [chi][s][t]
+  std::vector<double> mat[dwf::MK_COUNT];
+  // device matrices per arithmetic precision (0: double, 1: float), kernel order
+  void *dmat[2][dwf::MK_COUNT] = {};
+  int *d_nbr[2] = {nullptr, nullptr};
+  double *d_U = nullptr;  // FP64 host-layout copy of the gauge field
+  void *d_gauge[4][2] = {};
+  bool gauge_loaded = false;
+  bool gauge_ready[4] = {false, false, false, false};
+  std::map<std::string, dwf::Buf> bufs;
+  dwf::CGScalars *d_sc = nullptr;
+  dwf::CGScalars *h_sc = nullptr;  // pinned mirror
+  double *d_part = nullptr;
+  unsigned *d_ticket = nullptr;
+  size_t part_len = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  int device = 0;
+  long long launches = 0;
+  // profiling of the current call
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<dwf::ProfRec> prof;
+  std::string err;
+};

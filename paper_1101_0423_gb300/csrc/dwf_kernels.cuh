@@ -1,0 +1,607 @@
+// dwf_kernels.cuh -- kernel templates of the domain-wall solver (sm_103a).
+//
+// Kernels (the paper's five catalogs of Sec. 3, re-designed):
+//   k_hop    Eq. 12 hopping block on every s-slice, links staged once per CTA in shared
+//            memory by a TMA bulk copy and reused by the Ns threads of a site (Sec. 3.2),
+//            with fused epilogues: M5 (Sec. 3.3), vector add/sub (Sec. 3.5), CG update and
+//            the block partial sums of the reductions (Sec. 3.4).
+//   k_smix   per-site matrices along s (M5, M5^T, S1, S2, omega + sigma L, ...), with the
+//            CG direction update p = r + beta p fused in front.
+//   k_pack / k_unpack  host layout <-> device layout (Sec. 3.1), precision conversion.
+//   k_norm2, k_accum, k_convert  reductions and vector updates.
+// Reductions: per-thread partials promoted to FP64, warp shuffles, block sums written to
+// a partials array; the last block to finish (atomic ticket) sums the partials in a fixed
+// order, so every result is deterministic and stays on the device.
+#pragma once
+
+#include "dwf_device.cuh"
+
+namespace dwf {
+
+// ------------------------------------------------------------------ TMA bulk copy + mbarrier
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// bounded wait on phase `ph`; false if the bound ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t ph, uint32_t max_tries) {
+  for (uint32_t i = 0; i < max_tries; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(ph)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+constexpr uint32_t kWaitTries = 1u << 20;  // each try_wait suspends for a bounded time
+
+enum { ERR_TMA_TIMEOUT = 1 };
+
+// ------------------------------------------------------------------ reductions
+
+// sum over the first `nact` lanes of a warp (lanes >= nact may not exist: the block size
+// need not be a multiple of 32); result valid in lane 0
+__device__ __forceinline__ double warp_sum(double v, int nact) {
+  const int lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
+  const unsigned mask = nact >= 32 ? 0xffffffffu : ((1u << nact) - 1u);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_down_sync(mask, v, o);
+    if (lane + o < nact) v += t;
+  }
+  return v;
+}
+
+// sum over the block (result valid in thread 0); `ws` holds >= 32 doubles
+__device__ __forceinline__ double block_sum(double v, double *ws) {
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthr = blockDim.x * blockDim.y;
+  const int nw = (nthr + 31) >> 5;
+  v = warp_sum(v, min(32, nthr - (tid & ~31)));
+  __syncthreads();
+  if ((tid & 31) == 0) ws[tid >> 5] = v;
+  __syncthreads();
+  double r = 0;
+  if (tid < 32) {
+    r = tid < nw ? ws[tid] : 0.0;
+    r = warp_sum(r, 32);
+  }
+  return r;
+}
+
+// which scalar the last block writes
+enum { FIN_NONE = 0, FIN_RED = 1, FIN_RED2 = 2, FIN_QQ = 3, FIN_CG = 4 };
+
+__device__ __forceinline__ void finish(int fin, double tot, CGScalars *sc) {
+  if (fin == FIN_RED) sc->red = tot;
+  else if (fin == FIN_RED2) sc->red2 = tot;
+  else if (fin == FIN_QQ) sc->qq = tot;
+  else if (fin == FIN_CG) {
+    // end of one CG iteration (Algorithm 1): beta = (r_new, r_new) / (r, r)
+    const double rr_new = tot;
+    sc->beta = rr_new / sc->rr;
+    sc->rr_old = sc->rr;
+    sc->rr = rr_new;
+    sc->iter += 1;
+    if (rr_new > sc->rmax2) sc->rmax2 = rr_new;
+    // reliable update due (Sec. 2.3): residual fell by delta, reached the target, the
+    // iteration cap, or stopped being a number
+    if (!(rr_new > sc->delta2 * sc->rmax2) || !(rr_new > sc->target2) || sc->iter >= sc->iter_cap)
+      sc->restart_flag = 1;
+  }
+}
+
+// grid-wide deterministic sum; every thread of every block must call it
+__device__ __forceinline__ void grid_sum(double v, double *partials, unsigned *ticket, int fin,
+                                         CGScalars *sc) {
+  __shared__ double ws[32];
+  __shared__ int am_last;
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthr = blockDim.x * blockDim.y;
+  double bs = block_sum(v, ws);
+  if (tid == 0) {
+    partials[blockIdx.x] = bs;
+    __threadfence();
+    unsigned t = atomicAdd(ticket, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (am_last) {
+    __threadfence();
+    double s = 0;
+    for (unsigned i = tid; i < gridDim.x; i += nthr) s += __ldcg(partials + i);
+    double tot = block_sum(s, ws);
+    if (tid == 0) {
+      finish(fin, tot, sc);
+      *ticket = 0u;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ hop kernel
+
+// epilogues of k_hop (H = raw hopping sum, D = -H/2; K = matrix along s, coefficient folded in)
+enum {
+  E_PLAIN = 0,     // out = coef H
+  E_M = 1,         // out = K H
+  E_XPAY_G5 = 2,   // out = y + coef g5 H, |out|^2 -> fin
+  E_XPAY = 3,      // out = y + coef H
+  E_M_XPAY = 4,    // out = y + K H
+  E_CG_UPDATE = 5, // Ap = y + K H; r -= alpha Ap; x += alpha p; |r|^2 -> FIN_CG
+  E_RESID = 6      // out = b - (y + K H), |out|^2 -> fin
+};
+
+template <int EPI> struct EpiT {
+  static constexpr bool has_m = EPI == E_M || EPI == E_M_XPAY || EPI == E_CG_UPDATE || EPI == E_RESID;
+  static constexpr bool has_red = EPI == E_XPAY_G5 || EPI == E_CG_UPDATE || EPI == E_RESID;
+};
+
+struct HopArgs {
+  Field in, out, y, b, r, x, p;
+  const void *gauge;   // doubled gauge of the output parity: [cb][8][LREALS]
+  const int *nbr;      // [cb][8] for the output parity
+  const void *K;       // matrix along s in kernel order K[chi][t][s] (precision real)
+  double coef;         // scale of H (plain/xpay) or of K (matrix epilogues)
+  long h;              // sites per parity
+  int Ns;
+  int fin;             // FIN_* of the reduction
+  int use_flag;        // honour CGScalars::restart_flag (skip work once set)
+  CGScalars *sc;
+  double *partials;
+  unsigned *ticket;
+};
+
+// dynamic shared memory layout of k_hop (bytes): [mbarrier 16][links][K][stage buffer]
+template <int P>
+__host__ __device__ inline size_t hop_link_bytes(int spb) {
+  return (size_t)spb * 8 * PT<P>::LREALS * sizeof(typename PT<P>::lreal);
+}
+template <int P>
+__host__ __device__ inline size_t hop_smem_bytes(int spb, int Ns, bool has_m) {
+  size_t b = 16 + ((hop_link_bytes<P>(spb) + 15) & ~size_t(15));
+  if (has_m) {
+    b += (size_t)2 * Ns * Ns * sizeof(typename PT<P>::real);
+    b = (b + 15) & ~size_t(15);
+    b += (size_t)spb * Ns * 24 * sizeof(typename PT<P>::real);
+  }
+  return b;
+}
+
+template <int P, int EPI>
+__global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
+  using T = PT<P>;
+  using R = typename T::real;
+  using E = EpiT<EPI>;
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int Ns = a.Ns;
+  const int s = threadIdx.x, sl = threadIdx.y, spb = blockDim.y;
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthr = blockDim.x * blockDim.y;
+  const long cb0 = (long)blockIdx.x * spb;
+  const int nsite = (int)min((long)spb, a.h - cb0);
+  const bool active = sl < nsite;
+  const long cb = cb0 + sl;
+
+  if (a.use_flag && a.sc->restart_flag) return;  // uniform over the grid
+
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+  typename T::lreal *sL = reinterpret_cast<typename T::lreal *>(sm + 16);
+  R *sK = reinterpret_cast<R *>(sm + 16 + ((hop_link_bytes<P>(spb) + 15) & ~size_t(15)));
+  R *sB = reinterpret_cast<R *>(reinterpret_cast<unsigned char *>(sK) +
+                                (((size_t)2 * Ns * Ns * sizeof(R) + 15) & ~size_t(15)));
+
+  // stage this CTA's links: one TMA bulk copy of nsite * 8 links (contiguous, 16-byte sized)
+  if (tid == 0) mbar_init(bar, 1);
+  __syncthreads();
+  const uint32_t lbytes = (uint32_t)(nsite * 8 * T::LREALS * sizeof(typename T::lreal));
+  if (tid == 0) {
+    mbar_expect_tx(bar, lbytes);
+    bulk_g2s(sL, static_cast<const typename T::lreal *>(a.gauge) + (size_t)cb0 * 8 * T::LREALS, lbytes, bar);
+  }
+  if constexpr (E::has_m) {
+    const R *Kg = static_cast<const R *>(a.K);
+    for (int i = tid; i < 2 * Ns * Ns; i += nthr) sK[i] = (R)a.coef * Kg[i];
+  }
+  int nb[8];
+  if (active) {
+#pragma unroll
+    for (int d = 0; d < 8; ++d) nb[d] = __ldg(a.nbr + cb * 8 + d);
+  }
+  const bool ok = mbar_wait(bar, 0, kWaitTries);
+  if (!ok) {
+    if (tid == 0) atomicExch(&a.sc->error, ERR_TMA_TIMEOUT);
+    mbar_wait(bar, 0, kWaitTries);  // give an in-flight copy a bounded time to land
+    return;
+  }
+  if constexpr (E::has_m) __syncthreads();  // sK visible
+
+  R acc[24];
+#pragma unroll
+  for (int c = 0; c < 24; ++c) acc[c] = 0;
+  if (active) {
+    const typename T::lreal *myL = sL + (size_t)sl * 8 * T::LREALS;
+    R ps[24], W[18];
+    load_sp_ro<P>(a.in, nb[0], s, Ns, ps); load_link<P>(myL + 0 * T::LREALS, W); hop_dir<0, -1>(acc, ps, W);
+    load_sp_ro<P>(a.in, nb[1], s, Ns, ps); load_link<P>(myL + 1 * T::LREALS, W); hop_dir<1, -1>(acc, ps, W);
+    load_sp_ro<P>(a.in, nb[2], s, Ns, ps); load_link<P>(myL + 2 * T::LREALS, W); hop_dir<2, -1>(acc, ps, W);
+    load_sp_ro<P>(a.in, nb[3], s, Ns, ps); load_link<P>(myL + 3 * T::LREALS, W); hop_dir<3, -1>(acc, ps, W);
+    load_sp_ro<P>(a.in, nb[4], s, Ns, ps); load_link<P>(myL + 4 * T::LREALS, W); hop_dir<0, 1>(acc, ps, W);
+    load_sp_ro<P>(a.in, nb[5], s, Ns, ps); load_link<P>(myL + 5 * T::LREALS, W); hop_dir<1, 1>(acc, ps, W);
+    load_sp_ro<P>(a.in, nb[6], s, Ns, ps); load_link<P>(myL + 6 * T::LREALS, W); hop_dir<2, 1>(acc, ps, W);
+    load_sp_ro<P>(a.in, nb[7], s, Ns, ps); load_link<P>(myL + 7 * T::LREALS, W); hop_dir<3, 1>(acc, ps, W);
+  }
+
+  if constexpr (E::has_m) {
+    // M5-type epilogue (Sec. 3.3): out_s = sum_t K_{st} H_t per chirality; the Ns slices
+    // of a site are in this CTA, staged through shared memory
+    R *mine = sB + ((size_t)sl * Ns + s) * 24;
+#pragma unroll
+    for (int c = 0; c < 24; ++c) mine[c] = acc[c];
+    __syncthreads();
+    if (active) {
+      const R *site = sB + (size_t)sl * Ns * 24;
+#pragma unroll
+      for (int c = 0; c < 24; ++c) acc[c] = 0;
+      for (int t = 0; t < Ns; ++t) {
+        const R kp = sK[t * Ns + s];              // K+[s][t]
+        const R km = sK[Ns * Ns + t * Ns + s];    // K-[s][t]
+        const R *v = site + t * 24;
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] += kp * v[c];
+#pragma unroll
+        for (int c = 12; c < 24; ++c) acc[c] += km * v[c];
+      }
+    }
+  }
+
+  double part = 0;
+  if (active) {
+    if constexpr (EPI == E_PLAIN) {
+#pragma unroll
+      for (int c = 0; c < 24; ++c) acc[c] *= (R)a.coef;
+      store_sp<P>(a.out, cb, s, Ns, acc);
+    } else if constexpr (EPI == E_M) {
+      store_sp<P>(a.out, cb, s, Ns, acc);
+    } else if constexpr (EPI == E_XPAY_G5 || EPI == E_XPAY) {
+      R y[24];
+      load_sp<P>(a.y, cb, s, Ns, y);
+      const R cf = (R)a.coef;
+      R pr = 0;
+#pragma unroll
+      for (int c = 0; c < 24; ++c) {
+        const R g = (EPI == E_XPAY_G5 && c >= 12) ? -cf : cf;
+        y[c] += g * acc[c];
+        pr += y[c] * y[c];
+      }
+      store_sp<P>(a.out, cb, s, Ns, y);
+      part = (double)pr;
+    } else if constexpr (EPI == E_M_XPAY) {
+      R y[24];
+      load_sp<P>(a.y, cb, s, Ns, y);
+#pragma unroll
+      for (int c = 0; c < 24; ++c) y[c] += acc[c];
+      store_sp<P>(a.out, cb, s, Ns, y);
+    } else if constexpr (EPI == E_CG_UPDATE) {
+      // Algorithm 1: alpha = (r, r) / (p, A p) with (p, A p) = |C^dag p|^2
+      const R alpha = (R)(a.sc->rr / a.sc->qq);
+      R y[24], r[24], xx[24], pp[24];
+      load_sp<P>(a.y, cb, s, Ns, y);
+      load_sp<P>(a.r, cb, s, Ns, r);
+      load_sp<P>(a.x, cb, s, Ns, xx);
+      load_sp<P>(a.p, cb, s, Ns, pp);
+      R pr = 0;
+#pragma unroll
+      for (int c = 0; c < 24; ++c) {
+        const R ap = y[c] + acc[c];
+        r[c] -= alpha * ap;
+        xx[c] += alpha * pp[c];
+        pr += r[c] * r[c];
+      }
+      store_sp<P>(a.r, cb, s, Ns, r);
+      store_sp<P>(a.x, cb, s, Ns, xx);
+      part = (double)pr;
+    } else if constexpr (EPI == E_RESID) {
+      R y[24], bb[24];
+      load_sp<P>(a.y, cb, s, Ns, y);
+      load_sp<P>(a.b, cb, s, Ns, bb);
+      R pr = 0;
+#pragma unroll
+      for (int c = 0; c < 24; ++c) {
+        bb[c] -= y[c] + acc[c];
+        pr += bb[c] * bb[c];
+      }
+      store_sp<P>(a.out, cb, s, Ns, bb);
+      part = (double)pr;
+    }
+  }
+  if constexpr (E::has_red) grid_sum(part, a.partials, a.ticket, a.fin, a.sc);
+}
+
+// ------------------------------------------------------------------ s-mixing kernel
+
+enum {
+  S_PLAIN = 0,  // out = K in
+  S_G5 = 1,     // out = K g5 in
+  S_CGP = 2,    // p = r + beta p (stored); out = K g5 p
+  S_DUAL = 3    // out = K in; out2 = K2 in
+};
+
+struct SmixArgs {
+  Field in, out, out2, r, p;
+  const void *K, *K2;  // K[chi][t][s]
+  double coef;
+  long h;
+  int Ns;
+  int use_flag;
+  CGScalars *sc;
+};
+
+template <int P>
+__host__ __device__ inline size_t smix_smem_bytes(int spb, int Ns, bool dual) {
+  size_t b = (size_t)(dual ? 4 : 2) * Ns * Ns * sizeof(typename PT<P>::real);
+  b = (b + 15) & ~size_t(15);
+  return b + (size_t)spb * Ns * 24 * sizeof(typename PT<P>::real);
+}
+
+template <int P, int MODE>
+__global__ void __launch_bounds__(256) k_smix(const SmixArgs a) {
+  using R = typename PT<P>::real;
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int Ns = a.Ns;
+  const int s = threadIdx.x, sl = threadIdx.y, spb = blockDim.y;
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nthr = blockDim.x * blockDim.y;
+  const long cb = (long)blockIdx.x * spb + sl;
+  const bool active = cb < a.h;
+  if (a.use_flag && a.sc->restart_flag) return;
+  constexpr bool dual = MODE == S_DUAL;
+  R *sK = reinterpret_cast<R *>(sm);
+  R *sB = reinterpret_cast<R *>(sm + ((((size_t)(dual ? 4 : 2) * Ns * Ns * sizeof(R)) + 15) & ~size_t(15)));
+  {
+    const R *Kg = static_cast<const R *>(a.K);
+    for (int i = tid; i < 2 * Ns * Ns; i += nthr) sK[i] = (R)a.coef * Kg[i];
+    if constexpr (dual) {
+      const R *K2 = static_cast<const R *>(a.K2);
+      for (int i = tid; i < 2 * Ns * Ns; i += nthr) sK[2 * Ns * Ns + i] = (R)a.coef * K2[i];
+    }
+  }
+  R v[24];
+  if (active) {
+    if constexpr (MODE == S_CGP) {
+      R r[24];
+      const R beta = (R)a.sc->beta;
+      load_sp<P>(a.r, cb, s, Ns, r);
+      load_sp<P>(a.p, cb, s, Ns, v);
+#pragma unroll
+      for (int c = 0; c < 24; ++c) v[c] = r[c] + beta * v[c];
+      store_sp<P>(a.p, cb, s, Ns, v);
+    } else {
+      load_sp_ro<P>(a.in, cb, s, Ns, v);
+    }
+    if constexpr (MODE == S_CGP || MODE == S_G5) {
+#pragma unroll
+      for (int c = 12; c < 24; ++c) v[c] = -v[c];
+    }
+    R *mine = sB + ((size_t)sl * Ns + s) * 24;
+#pragma unroll
+    for (int c = 0; c < 24; ++c) mine[c] = v[c];
+  }
+  __syncthreads();
+  if (!active) return;
+  const R *site = sB + (size_t)sl * Ns * 24;
+  for (int which = 0; which < (dual ? 2 : 1); ++which) {
+    const R *K = sK + which * 2 * Ns * Ns;
+    R o[24];
+#pragma unroll
+    for (int c = 0; c < 24; ++c) o[c] = 0;
+    for (int t = 0; t < Ns; ++t) {
+      const R kp = K[t * Ns + s], km = K[Ns * Ns + t * Ns + s];
+      const R *vv = site + t * 24;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) o[c] += kp * vv[c];
+#pragma unroll
+      for (int c = 12; c < 24; ++c) o[c] += km * vv[c];
+    }
+    store_sp<P>(which == 0 ? a.out : a.out2, cb, s, Ns, o);
+  }
+}
+
+// ------------------------------------------------------------------ per-(site, s) vector kernels
+
+struct VecArgs {
+  Field a, b, c;     // operands (meaning per kernel)
+  long n;            // h * Ns
+  int Ns;
+  double coef;
+  int fin;
+  CGScalars *sc;
+  double *partials;
+  unsigned *ticket;
+};
+
+// |a|^2 -> fin (precision P)
+template <int P>
+__global__ void __launch_bounds__(256) k_norm2(const VecArgs v) {
+  using R = typename PT<P>::real;
+  double part = 0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < v.n; i += (long)gridDim.x * blockDim.x) {
+    R x[24];
+    load_sp_ro<P>(v.a, i / v.Ns, (int)(i % v.Ns), v.Ns, x);
+    R pr = 0;
+#pragma unroll
+    for (int c = 0; c < 24; ++c) pr += x[c] * x[c];
+    part += (double)pr;
+  }
+  grid_sum(part, v.partials, v.ticket, v.fin, v.sc);
+}
+
+// b (precision PB) = a (precision PA), element-wise with the layout conversion
+template <int PA, int PB>
+__global__ void __launch_bounds__(256) k_convert(const VecArgs v) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < v.n; i += (long)gridDim.x * blockDim.x) {
+    const long cb = i / v.Ns;
+    const int s = (int)(i % v.Ns);
+    typename PT<PA>::real x[24];
+    load_sp_ro<PA>(v.a, cb, s, v.Ns, x);
+    typename PT<PB>::real y[24];
+#pragma unroll
+    for (int c = 0; c < 24; ++c) y[c] = (typename PT<PB>::real)x[c];
+    store_sp<PB>(v.b, cb, s, v.Ns, y);
+  }
+}
+
+// FP64 a += (precision P) b; b = 0  (x_hat += x at a restart, Algorithm 2)
+template <int P>
+__global__ void __launch_bounds__(256) k_accum(const VecArgs v) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < v.n; i += (long)gridDim.x * blockDim.x) {
+    const long cb = i / v.Ns;
+    const int s = (int)(i % v.Ns);
+    double xa[24];
+    typename PT<P>::real xb[24];
+    load_sp<P_F64>(v.a, cb, s, v.Ns, xa);
+    load_sp<P>(v.b, cb, s, v.Ns, xb);
+#pragma unroll
+    for (int c = 0; c < 24; ++c) { xa[c] += (double)xb[c]; xb[c] = 0; }
+    store_sp<P_F64>(v.a, cb, s, v.Ns, xa);
+    store_sp<P>(v.b, cb, s, v.Ns, xb);
+  }
+}
+
+// ------------------------------------------------------------------ layout conversion (Sec. 3.1)
+
+struct Geom {
+  int d[4];     // Nx, Ny, Nz, Nt
+  long h;       // V4 / 2
+  int Ns;
+};
+
+// lexicographic site of checkerboard index cb in parity p
+__device__ __forceinline__ long cb_to_site(const Geom &g, long cb, int p, int (&c)[4]) {
+  const int hx = g.d[0] >> 1;
+  long r = cb;
+  const int xh = (int)(r % hx); r /= hx;
+  c[1] = (int)(r % g.d[1]); r /= g.d[1];
+  c[2] = (int)(r % g.d[2]); r /= g.d[2];
+  c[3] = (int)r;
+  c[0] = 2 * xh + ((p + c[1] + c[2] + c[3]) & 1);
+  return c[0] + (long)g.d[0] * (c[1] + (long)g.d[1] * (c[2] + (long)g.d[2] * c[3]));
+}
+
+// device copy of the host layout (FP64, full lattice) -> parity p in precision P
+template <int P>
+__global__ void __launch_bounds__(256) k_pack(const double *host, Field out, Geom g, int p) {
+  const long n = g.h * g.Ns;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const long cb = i / g.Ns;
+    const int s = (int)(i % g.Ns);
+    int c[4];
+    const long site = cb_to_site(g, cb, p, c);
+    const double2 *src = reinterpret_cast<const double2 *>(host + ((size_t)site * g.Ns + s) * 24);
+    typename PT<P>::real v[24];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 t = __ldg(src + k);
+      v[2 * k] = (typename PT<P>::real)t.x;
+      v[2 * k + 1] = (typename PT<P>::real)t.y;
+    }
+    store_sp<P>(out, cb, s, g.Ns, v);
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_unpack(Field in, double *host, Geom g, int p) {
+  const long n = g.h * g.Ns;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const long cb = i / g.Ns;
+    const int s = (int)(i % g.Ns);
+    int c[4];
+    const long site = cb_to_site(g, cb, p, c);
+    typename PT<P>::real v[24];
+    load_sp_ro<P>(in, cb, s, g.Ns, v);
+    double2 *dst = reinterpret_cast<double2 *>(host + ((size_t)site * g.Ns + s) * 24);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) dst[k] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
+  }
+}
+
+// doubled gauge field of output parity p from the FP64 host layout
+template <int P>
+__global__ void k_gauge(const double *U, typename PT<P>::lreal *G, Geom g, int p) {
+  using L = typename PT<P>::lreal;
+  constexpr int LR = PT<P>::LREALS;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < g.h * 8; i += (long)gridDim.x * blockDim.x) {
+    const long cb = i >> 3;
+    const int dir = (int)(i & 7);
+    const int mu = dir & 3;
+    int c[4];
+    long site = cb_to_site(g, cb, p, c);
+    bool dag = false;
+    if (dir >= 4) {
+      c[mu] = (c[mu] + g.d[mu] - 1) % g.d[mu];
+      site = c[0] + (long)g.d[0] * (c[1] + (long)g.d[1] * (c[2] + (long)g.d[2] * c[3]));
+      dag = true;
+    }
+    const double *u = U + ((size_t)site * 4 + mu) * 18;
+    L *o = G + (size_t)i * LR;
+    for (int a = 0; a < 3 && a * 6 < LR; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double re = dag ? u[2 * (3 * b + a)] : u[2 * (3 * a + b)];
+        double im = dag ? -u[2 * (3 * b + a) + 1] : u[2 * (3 * a + b) + 1];
+        if constexpr (P == P_F64) { o[2 * (3 * a + b)] = re; o[2 * (3 * a + b) + 1] = im; }
+        else if constexpr (P == P_F32) { o[2 * (3 * a + b)] = (float)re; o[2 * (3 * a + b) + 1] = (float)im; }
+        else if constexpr (P == P_F16) { o[2 * (3 * a + b)] = __double2half(re); o[2 * (3 * a + b) + 1] = __double2half(im); }
+        else { o[2 * (3 * a + b)] = __double2bfloat16(re); o[2 * (3 * a + b) + 1] = __double2bfloat16(im); }
+      }
+  }
+}
+
+#ifdef DWF_DEFINE_PLAIN_KERNELS  // non-template kernels: defined in one translation unit only
+
+// |a - b|^2 (both FP64) -> fin
+__global__ void __launch_bounds__(256) k_diff_norm2(const VecArgs v) {
+  double part = 0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < v.n; i += (long)gridDim.x * blockDim.x) {
+    double x[24], y[24];
+    load_sp_ro<P_F64>(v.a, i / v.Ns, (int)(i % v.Ns), v.Ns, x);
+    load_sp_ro<P_F64>(v.b, i / v.Ns, (int)(i % v.Ns), v.Ns, y);
+    for (int c = 0; c < 24; ++c) part += (x[c] - y[c]) * (x[c] - y[c]);
+  }
+  grid_sum(part, v.partials, v.ticket, v.fin, v.sc);
+}
+
+// neighbour table of output parity p: nbr[cb][dir]
+__global__ void k_neighbours(int *nbr, Geom g, int p) {
+  for (long cb = (long)blockIdx.x * blockDim.x + threadIdx.x; cb < g.h; cb += (long)gridDim.x * blockDim.x) {
+    int c[4];
+    cb_to_site(g, cb, p, c);
+    for (int dir = 0; dir < 8; ++dir) {
+      const int mu = dir & 3;
+      int e[4] = {c[0], c[1], c[2], c[3]};
+      e[mu] = (e[mu] + (dir < 4 ? 1 : g.d[mu] - 1)) % g.d[mu];
+      const long site = e[0] + (long)g.d[0] * (e[1] + (long)g.d[1] * (e[2] + (long)g.d[2] * e[3]));
+      nbr[cb * 8 + dir] = (int)(site >> 1);
+    }
+  }
+}
+
+#endif
+
+}  // namespace dwf

@@ -1,0 +1,229 @@
+"""Thin ctypes binding of the C-ABI in include/dwf.h (argument marshalling only).
+
+Every function keeps the C name.  Host arrays are float64 numpy arrays in the host
+layouts of include/dwf.h; the ``*_dev`` functions take device pointers (ints, or any
+object with ``data_ptr()`` such as a torch CUDA tensor) and an optional CUDA stream
+(an int handle or an object with ``cuda_stream``).  Errors raise :class:`DwfError`
+carrying the status and the library's message.  There is no CPU fallback: if the
+CUDA library cannot be built or loaded, :func:`load` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdwf_gb300.so")
+
+OP_DEO, OP_DOE, OP_M5, OP_M5T, OP_C, OP_CDAG, OP_CCDAG, OP_DFULL, OP_DW = range(9)
+PREC_F64, PREC_F32, PREC_F16, PREC_BF16 = range(4)
+MODE_AUTO, MODE_RELIABLE, MODE_DEFECT = range(3)
+SYS_FULL, SYS_NORMAL = range(2)
+KC_NAMES = ["hop_m5", "hop_xpay", "hop_update", "smix_p", "f64", "other"]
+STATUS = ["DWF_OK", "DWF_EINVAL", "DWF_ENOMEM", "DWF_ENOCONV", "DWF_EBUSY", "DWF_EAGAIN",
+          "DWF_ETIMEOUT", "DWF_ECUDA", "DWF_ENOGAUGE"]
+DWF_OK, DWF_EINVAL, DWF_ENOMEM, DWF_ENOCONV, DWF_EBUSY, DWF_EAGAIN, DWF_ETIMEOUT, DWF_ECUDA, \
+    DWF_ENOGAUGE = range(9)
+
+
+class DwfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        super().__init__(f"{STATUS[status] if 0 <= status < len(STATUS) else status}: {msg}")
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("delta", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("inner_prec", ctypes.c_int), ("mode", ctypes.c_int), ("system", ctypes.c_int),
+                ("schur_parity", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("profile", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("mode_used", ctypes.c_int),
+                ("converged", ctypes.c_int), ("true_res", ctypes.c_double),
+                ("true_res_full", ctypes.c_double), ("flops", ctypes.c_double),
+                ("time_ms", ctypes.c_double), ("class_ms", ctypes.c_double * 6),
+                ("class_launches", ctypes.c_int * 6), ("kernel_launches", ctypes.c_longlong),
+                ("bytes_hop_m5", ctypes.c_double), ("reserved", ctypes.c_double * 3)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("class_ms", "class_launches", "reserved")}
+        d["class_ms"] = {n: self.class_ms[i] for i, n in enumerate(KC_NAMES)}
+        d["class_launches"] = {n: self.class_launches[i] for i, n in enumerate(KC_NAMES)}
+        return d
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load libdwf_gb300.so (building it with nvcc first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library missing: {LIB_PATH}")
+        from . import build as _build
+        _build.build()
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    i, d = ctypes.c_int, ctypes.c_double
+    sig = {
+        "dwf_create": ([ip, i, d, d, dp, dp, ctypes.POINTER(vp)], i),
+        "dwf_destroy": ([vp], i),
+        "dwf_load_gauge": ([vp, dp], i),
+        "dwf_load_gauge_dev": ([vp, vp, vp], i),
+        "dwf_apply_eo": ([vp, i, i, i, dp, dp], i),
+        "dwf_apply_eo_dev": ([vp, i, i, i, vp, vp, vp], i),
+        "dwf_solve": ([vp, dp, dp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats)], i),
+        "dwf_solve_dev": ([vp, vp, vp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), vp], i),
+        "dwf_last_error": ([vp], ctypes.c_char_p),
+        "dwf_status_string": ([i], ctypes.c_char_p),
+        "dwf_solve_params_default": ([ctypes.POINTER(SolveParams)], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError("expected a device pointer (int) or an object with data_ptr()")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(ctx, st):
+    if st != DWF_OK:
+        msg = load().dwf_last_error(ctx).decode() if ctx else ""
+        raise DwfError(st, msg)
+
+
+def dwf_solve_params_default() -> SolveParams:
+    p = SolveParams()
+    load().dwf_solve_params_default(ctypes.byref(p))
+    return p
+
+
+def dwf_create(dims, Ns, m0, mq, omega, sigma):
+    """Returns an opaque context handle (int)."""
+    lib = load()
+    omega, sigma = _f64(omega), _f64(sigma)
+    out = ctypes.c_void_p()
+    st = lib.dwf_create((ctypes.c_int * 4)(*[int(v) for v in dims]), int(Ns), float(m0), float(mq),
+                        _dp(omega), _dp(sigma), ctypes.byref(out))
+    if st != DWF_OK:
+        raise DwfError(st, "dwf_create rejected its arguments or could not allocate")
+    return out.value
+
+
+def dwf_destroy(ctx):
+    _check(None, load().dwf_destroy(ctx))
+
+
+def dwf_load_gauge(ctx, U):
+    U = _f64(U)
+    _check(ctx, load().dwf_load_gauge(ctx, _dp(U)))
+
+
+def dwf_load_gauge_dev(ctx, d_U, stream=None):
+    _check(ctx, load().dwf_load_gauge_dev(ctx, _ptr(d_U), _stream(stream)))
+
+
+def dwf_apply_eo(ctx, op, prec, parity, x) -> np.ndarray:
+    x = _f64(x)
+    out = np.empty_like(x)
+    _check(ctx, load().dwf_apply_eo(ctx, int(op), int(prec), int(parity), _dp(x), _dp(out)))
+    return out
+
+
+def dwf_apply_eo_dev(ctx, op, prec, parity, d_in, d_out, stream=None):
+    _check(ctx, load().dwf_apply_eo_dev(ctx, int(op), int(prec), int(parity), _ptr(d_in), _ptr(d_out),
+                                        _stream(stream)))
+
+
+def _params(params=None, **kw) -> SolveParams:
+    p = dwf_solve_params_default() if params is None else params
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def dwf_solve(ctx, rhs, params=None, allow_noconv=False, **kw):
+    """Returns (solution array, stats dict).  Keyword arguments override params fields."""
+    rhs = _f64(rhs)
+    sol = np.empty_like(rhs)
+    p = _params(params, **kw)
+    stats = SolveStats()
+    st = load().dwf_solve(ctx, _dp(rhs), _dp(sol), ctypes.byref(p), ctypes.byref(stats))
+    if not (allow_noconv and st == DWF_ENOCONV):
+        _check(ctx, st)
+    return sol, stats.as_dict()
+
+
+def dwf_solve_dev(ctx, d_rhs, d_sol, params=None, stream=None, allow_noconv=False, **kw) -> dict:
+    p = _params(params, **kw)
+    stats = SolveStats()
+    st = load().dwf_solve_dev(ctx, _ptr(d_rhs), _ptr(d_sol), ctypes.byref(p), ctypes.byref(stats),
+                              _stream(stream))
+    if not (allow_noconv and st == DWF_ENOCONV):
+        _check(ctx, st)
+    return stats.as_dict()
+
+
+def dwf_last_error(ctx) -> str:
+    return load().dwf_last_error(ctx).decode()
+
+
+class Context:
+    """Owns a dwf_ctx; closes it on exit."""
+
+    def __init__(self, dims, Ns, m0, mq, omega, sigma, U=None):
+        self.dims, self.Ns = tuple(dims), int(Ns)
+        self.h = dwf_create(dims, Ns, m0, mq, omega, sigma)
+        if U is not None:
+            dwf_load_gauge(self.h, U)
+
+    def close(self):
+        if self.h:
+            dwf_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,79 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every function that
+include/*.h declares, its structs have the sizes the binding assumes, and argument
+validation that happens before any CUDA call returns DWF_EINVAL."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1101_0423_gb300 import build, dwf
+    build.build()
+    return dwf.load()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(dwf_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["dwf_create", "dwf_destroy", "dwf_load_gauge", "dwf_apply_eo", "dwf_solve"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = os.path.join(ROOT, "paper_1101_0423_gb300", "libdwf_gb300.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    for n in declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    from paper_1101_0423_gb300 import dwf
+    src = tmp_path / "sz.c"
+    src.write_text('#include "dwf.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(dwf_solve_params), sizeof(dwf_solve_stats),'
+                   ' offsetof(dwf_solve_stats, kernel_launches), offsetof(dwf_solve_params, profile));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    sp, ss, off_kl, off_prof = map(int, subprocess.check_output([str(exe)]).split())
+    assert sp == ctypes.sizeof(dwf.SolveParams)
+    assert ss == ctypes.sizeof(dwf.SolveStats)
+    assert off_kl == dwf.SolveStats.kernel_launches.offset
+    assert off_prof == dwf.SolveParams.profile.offset
+
+
+def test_defaults_and_status_strings(lib):
+    from paper_1101_0423_gb300 import dwf
+    p = dwf.dwf_solve_params_default()
+    assert p.tol == 1e-10 and p.inner_prec == dwf.PREC_F32 and p.schur_parity == 1
+    assert lib.dwf_status_string(dwf.DWF_ENOCONV) == b"DWF_ENOCONV"
+
+
+@pytest.mark.parametrize("dims,ns,m0,omega_ok", [((3, 4, 4, 4), 4, 1.8, True), ((4, 4, 4, 4), 0, 1.8, True),
+                                                  ((4, 4, 4, 4), 4, 2.5, True), ((4, 4, 4, 4), 4, 1.8, False)])
+def test_create_rejects_invalid_arguments_before_touching_cuda(lib, dims, ns, m0, omega_ok):
+    from paper_1101_0423_gb300 import dwf
+    n = max(ns, 1)
+    om = np.ones(n) if omega_ok else -np.ones(n)
+    with pytest.raises(dwf.DwfError) as e:
+        dwf.dwf_create(dims, ns, m0, 0.05, om, np.zeros(n))
+    assert e.value.status == dwf.DWF_EINVAL
