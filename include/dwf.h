@@ -107,7 +107,9 @@ typedef struct {
     int check_every;   /* inner iterations between host polls of the device flags (default 8) */
     int use_graph;     /* capture each batch of inner iterations in a CUDA graph (default 1) */
     int profile;       /* record CUDA events around every kernel class (default 0) */
-    int reserved[6];
+    int stall_iters;   /* restart, resetting the search direction, when |r| has not reached a
+                          new minimum for this many inner iterations; <= 0 selects 500 */
+    int reserved[5];
 } dwf_solve_params;
 
 /* kernel classes timed when params.profile != 0 */

@@ -63,11 +63,18 @@ struct CGScalars {
   double target2;  // (tol |b|)^2
   double red;      // result slot of plain norm reductions
   double red2;
-  int restart_flag;  // set on device when an FP64 restart is due; kernels then skip work
+  double rr_start;  // |r|^2 at the last restart (divergence guard)
+  double rr_min;    // smallest |r|^2 since the last restart (stall guard)
+  int restart_flag;  // set on device when an FP64 restart is due (a RS_* reason); kernels then skip work
   int iter;          // inner iterations done
   int iter_cap;      // restart when iter reaches this
   int error;         // kernel error word (bounded wait gave up)
+  int iter_min;      // iteration at which rr_min was reached
+  int stall_iters;   // restart when rr_min has not improved for this many iterations
 };
+
+// reasons for an FP64 restart
+enum { RS_NONE = 0, RS_DELTA = 1, RS_TARGET = 2, RS_CAP = 3, RS_DIVERGED = 4, RS_STALLED = 5 };
 
 // ------------------------------------------------------------------ spinor access
 

@@ -7,6 +7,7 @@
 // batch of inner iterations, and a batch is replayed from a CUDA graph.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include <cmath>
 #include <string.h>
@@ -960,15 +961,16 @@ extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_s
   const double tol2 = prm.tol * prm.tol;
 
   int iters = 0, restarts = 0, mode_now = prm.mode == DWF_MODE_DEFECT ? DWF_MODE_DEFECT : DWF_MODE_RELIABLE;
-  double rhat2 = bnorm2, prev_rhat2 = bnorm2;
+  double rhat2 = bnorm2, prev_rhat2 = bnorm2, rr_last = 0.0;
+  int switches = 0;
+  const int stall_iters = prm.stall_iters > 0 ? prm.stall_iters : 500;
   bool converged = bnorm2 == 0.0;
   dwf_status result = DWF_OK;
   // (re)arm the inner CG after a restart: r already holds r_hat in the inner precision and
   // red2 = |r|^2.  Reliable updates keep p (beta from the recomputed residual), defect
   // correction restarts from p = r (beta = 0).
-  auto arm = [&](double tol_now, bool first) -> dwf_status {
+  auto arm = [&](double tol_now, bool first, bool reset_p, double rr_conv) -> dwf_status {
     CGScalars &h = *c->h_sc;
-    const double rr_conv = h.red2;
     if (first) {
       h.rr_old = rr_conv;
       h.qq = 1.0;
@@ -978,10 +980,14 @@ extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_s
       h.error = 0;
       h.delta2 = delta * delta;
     } else {
-      h.beta = (mode_now == DWF_MODE_DEFECT) ? 0.0 : rr_conv / h.rr_old;
+      h.beta = reset_p ? 0.0 : rr_conv / h.rr_old;
     }
     h.rr = rr_conv;
     h.rmax2 = rr_conv;
+    h.rr_start = rr_conv;
+    h.rr_min = rr_conv;
+    h.iter_min = h.iter;
+    h.stall_iters = stall_iters;
     h.target2 = tol_now * tol_now * bnorm2;
     h.restart_flag = 0;
     return push_scalars(c, st);
@@ -997,6 +1003,9 @@ extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_s
     }
   } graph_guard{gexec, graph};
   const bool use_graph = prm.use_graph && !c->profiling;
+  // DWF_TRACE=1 prints one line per FP64 restart to stderr
+  const char *trace_env = getenv("DWF_TRACE");
+  const bool trace = trace_env && trace_env[0] == '1';
   bool first_batch = true;
   // mixed-precision CG until |b - A x_hat| <= tol_now |b| (FP64)
   auto cg_loop = [&](double tol_now) -> dwf_status {
@@ -1026,13 +1035,19 @@ extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_s
       }
       first_batch = false;
       TRY(pull_scalars(c, st));
-      if (!c->h_sc->restart_flag) continue;
+      const int reason = c->h_sc->restart_flag;
+      if (!reason) continue;
       iters = c->h_sc->iter;
       // ---- reliable update / defect correction restart in FP64
       TRY(fp64_restart(c, st, S));
       TRY(pull_scalars(c, st));
       ++restarts;
       rhat2 = c->h_sc->red;
+      rr_last = c->h_sc->red2;
+      if (trace)
+        fprintf(stderr, "dwf: restart %d iter %d reason %d |r_iter|/|b| %.3e |r_true|/|b| %.3e mode %s\n", restarts,
+                iters, reason, sqrt(c->h_sc->rr / bnorm2), sqrt(rhat2 / bnorm2),
+                mode_now == DWF_MODE_DEFECT ? "defect" : "reliable");
       if (!std::isfinite(rhat2)) return fail(c, DWF_ENOCONV, "residual is not finite");
       if (rhat2 <= tol2 * bnorm2) {
         converged = true;
@@ -1040,10 +1055,14 @@ extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_s
       }
       if (iters >= prm.max_iter) return fail(c, DWF_ENOCONV, "max_iter reached");
       // Sec. 2.3: fall back to defect correction when the reliable updates stop converging
-      if (prm.mode == DWF_MODE_AUTO && mode_now == DWF_MODE_RELIABLE && rhat2 > prev_rhat2)
+      // (the true residual grew, or the inner recursion diverged or stalled)
+      const bool failed = rhat2 > prev_rhat2 || reason == RS_DIVERGED || reason == RS_STALLED;
+      if (prm.mode == DWF_MODE_AUTO && mode_now == DWF_MODE_RELIABLE && failed) {
         mode_now = DWF_MODE_DEFECT;
+        ++switches;
+      }
       prev_rhat2 = rhat2;
-      TRY(arm(tol_now, false));
+      TRY(arm(tol_now, false, mode_now == DWF_MODE_DEFECT || failed, rr_last));
     }
     return DWF_OK;
   };
@@ -1095,16 +1114,20 @@ extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_s
     return DWF_OK;
   };
 
-  TRY(arm(prm.tol, true));
-  result = cg_loop(prm.tol);
+  // the full-system residual runs a little above the Schur one (by at most cond(S1)), so the
+  // Schur system of a full solve aims at half the tolerance
+  const double tol_schur = full ? 0.5 * prm.tol : prm.tol;
+  rr_last = c->h_sc->red2;
+  TRY(arm(tol_schur, true, true, rr_last));
+  result = cg_loop(tol_schur);
   if (result == DWF_OK && full) {
     double res_full = 0;
     TRY(reconstruct(&res_full));
     // the full-system residual exceeds the Schur one by at most cond(S1); if it misses
     // the target, tighten the Schur tolerance once and continue from x_hat
     if (res_full > prm.tol && converged) {
-      const double tighter = prm.tol * std::min(0.1, 0.5 * prm.tol / res_full);
-      TRY(arm(tighter, false));
+      const double tighter = tol_schur * std::min(0.1, 0.5 * prm.tol / res_full);
+      TRY(arm(tighter, false, mode_now == DWF_MODE_DEFECT, rr_last));
       result = cg_loop(tighter);
       if (result == DWF_OK) TRY(reconstruct(&res_full));
     }

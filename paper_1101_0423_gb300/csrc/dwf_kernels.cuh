@@ -102,10 +102,18 @@ __device__ __forceinline__ void finish(int fin, double tot, CGScalars *sc) {
     sc->rr = rr_new;
     sc->iter += 1;
     if (rr_new > sc->rmax2) sc->rmax2 = rr_new;
-    // reliable update due (Sec. 2.3): residual fell by delta, reached the target, the
-    // iteration cap, or stopped being a number
-    if (!(rr_new > sc->delta2 * sc->rmax2) || !(rr_new > sc->target2) || sc->iter >= sc->iter_cap)
-      sc->restart_flag = 1;
+    if (rr_new < sc->rr_min) {
+      sc->rr_min = rr_new;
+      sc->iter_min = sc->iter;
+    }
+    // FP64 restart due (Sec. 2.3): the residual fell by delta (reliable update) or reached
+    // the target; or the iteration cap; or the recursion diverged, stalled or stopped
+    // being a number (then the host resets the search direction)
+    if (!(rr_new > sc->target2)) sc->restart_flag = RS_TARGET;
+    else if (!(rr_new > sc->delta2 * sc->rmax2)) sc->restart_flag = RS_DELTA;
+    else if (sc->iter >= sc->iter_cap) sc->restart_flag = RS_CAP;
+    else if (!(rr_new < 1e6 * sc->rr_start)) sc->restart_flag = RS_DIVERGED;
+    else if (sc->iter - sc->iter_min > sc->stall_iters) sc->restart_flag = RS_STALLED;
   }
 }
 

@@ -38,8 +38,8 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("delta", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("inner_prec", ctypes.c_int), ("mode", ctypes.c_int), ("system", ctypes.c_int),
                 ("schur_parity", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("profile", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("use_graph", ctypes.c_int), ("profile", ctypes.c_int), ("stall_iters", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class SolveStats(ctypes.Structure):
