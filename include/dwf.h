@@ -169,6 +169,29 @@ dwf_status dwf_apply_eo(dwf_ctx *ctx, int op, int prec, int parity, const double
 dwf_status dwf_apply_eo_dev(dwf_ctx *ctx, int op, int prec, int parity, const double *d_in,
                             double *d_out, void *stream);
 
+/* Allocation-free variant of dwf_apply_eo_dev (the paper has no counterpart: it is a
+ * service for callers that must not allocate device memory while they run -- code
+ * recording a CUDA stream capture, where cudaMalloc is not allowed; applications whose
+ * device memory is owned by their own pool allocator or held to a fixed budget; and
+ * latency-critical paths where a first-call allocation would stall).
+ * Applies DWF_OP_DEO, DOE, M5, M5T, C, CDAG or CCDAG exactly as dwf_apply_eo_dev does, with
+ * the same arguments, but takes every work field and the reduction scratch from one static
+ * device array of 64 MiB compiled into the library (held on every GPU that loads the
+ * library until the process exits) and calls no cudaMalloc, cudaFree or other allocating
+ * routine.  The caller still passes the input and output arrays.  Limits and behaviour:
+ *   - five work fields plus the partial sums must fit in 64 MiB: about 5 * 24 * Ns * V4/2
+ *     reals of the precision (FP32: Ns * V4/2 <= ~135,000; FP64: <= ~67,000, e.g. 8^4 x 16);
+ *     larger lattices return DWF_EINVAL with the byte count in dwf_last_error;
+ *   - the gauge field of `prec` must already exist (dwf_load_gauge builds FP64 and FP32; one
+ *     dwf_apply_eo_dev call builds a 16-bit form), else DWF_EINVAL;
+ *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture begins;
+ *   - every call shares the one array, which keeps the last call's contents; the call clears
+ *     what must start at zero itself.  Calls that overlap on the GPU (two streams, two
+ *     contexts, or two host threads) race on the array and must be serialised by the caller. */
+dwf_status dwf_apply_eo_dev_static(dwf_ctx *ctx, int op, int prec, int parity, const double *d_in,
+                                   double *d_out, void *stream);
+
 /* Solve.  DWF_SYS_FULL: rhs = eta, sol = psi (full-lattice host arrays) with D psi = eta.
  * DWF_SYS_NORMAL: rhs = b, sol = x on the sites of params->schur_parity with
  * C C^dag x = b (other sites of sol are set to 0).  params may be NULL (defaults);

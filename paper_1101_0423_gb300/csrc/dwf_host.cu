@@ -1179,3 +1179,152 @@ extern "C" dwf_status dwf_solve(dwf_ctx *c, const double *rhs, double *sol, cons
   CK(cudaStreamSynchronize(c->stream));
   return s;
 }
+
+// ====================================================================== allocation-free variant
+//
+// dwf_apply_eo_dev_static is dwf_apply_eo_dev for the Schur-parity operators with every
+// work field (packed input and output, three intermediates) and the reduction scratch
+// (block partial sums and the last-block ticket) taken from one static device array, so a
+// call never allocates.  It is for callers that must not allocate device memory while
+// they run: code recording a CUDA stream capture (cudaMalloc is not allowed while a
+// capture is open), applications whose device memory is owned by their own pool
+// allocator or held to a fixed budget, and latency-critical paths where a first-call
+// allocation would stall.  The array is a file-scope __device__ variable, so every GPU
+// that loads the library holds it until the process exits.
+
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)64 << 20;  // 64 MiB per device
+__device__ __align__(256) unsigned char g_dwf_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxStaticDevices = 256;
+void *g_static_scratch_addr[kMaxStaticDevices] = {};
+std::mutex g_static_scratch_mutex;
+
+// Device address of the static array on device `dev` (which must be current).  In host
+// code the array's name is only a host-side stand-in, so the address is looked up once per
+// device with cudaGetSymbolAddress and cached.
+cudaError_t static_scratch_address(int dev, void **out) {
+  std::lock_guard<std::mutex> lock(g_static_scratch_mutex);
+  if (!g_static_scratch_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_dwf_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_scratch_addr[dev] = p;
+  }
+  *out = g_static_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// points the context's reduction scratch at the static array for the duration of one call
+struct ReductionScratchSwap {
+  dwf_ctx *c;
+  double *part;
+  unsigned *ticket;
+  ReductionScratchSwap(dwf_ctx *c_, double *p, unsigned *t) : c(c_), part(c_->d_part), ticket(c_->d_ticket) {
+    c->d_part = p;
+    c->d_ticket = t;
+  }
+  ~ReductionScratchSwap() {
+    c->d_part = part;
+    c->d_ticket = ticket;
+  }
+};
+
+}  // namespace
+
+extern "C" dwf_status dwf_apply_eo_dev_static(dwf_ctx *c, int op, int prec, int parity, const double *d_in,
+                                              double *d_out, void *stream) {
+  TRY(check_ctx(c));
+  if (!d_in || !d_out || !aligned16(d_in) || !aligned16(d_out))
+    return fail(c, DWF_EINVAL, "null or non-16-byte-aligned field pointer");
+  if (!valid_prec(prec)) return fail(c, DWF_EINVAL, "unknown precision");
+  if (op < DWF_OP_DEO || op > DWF_OP_CCDAG)
+    return fail(c, DWF_EINVAL, "the allocation-free variant applies DEO, DOE, M5, M5T, C, CDAG or CCDAG");
+  const bool needs_parity = op >= DWF_OP_M5;
+  if (needs_parity && parity != 0 && parity != 1) return fail(c, DWF_EINVAL, "parity must be 0 or 1");
+  const size_t full = (size_t)c->V4 * c->Ns * 24 * sizeof(double);
+  if ((const char *)d_in < (const char *)d_out + full && (const char *)d_out < (const char *)d_in + full)
+    return fail(c, DWF_EINVAL, "in and out overlap");
+  if (!c->gauge_loaded) return fail(c, DWF_ENOGAUGE, "dwf_load_gauge has not been called");
+  if (!c->gauge_ready[prec])
+    return fail(c, DWF_EINVAL,
+                "the gauge field of this precision is not built yet (dwf_load_gauge builds FP64 and FP32; "
+                "one dwf_apply_eo_dev call in a 16-bit precision builds that form)");
+  if (c->device < 0 || c->device >= kMaxStaticDevices) return fail(c, DWF_EINVAL, "device ordinal too large");
+
+  // carve five fields, the partial sums and the ticket out of the static array
+  const size_t n = (size_t)c->h * c->Ns;
+  const size_t data_b = round256(n * site_bytes(prec));
+  const size_t nrm_b = prec >= P_F16 ? round256(n * sizeof(float)) : 0;
+  const long spb = sites_per_block(prec, c->Ns);
+  const size_t max_blocks = std::max<size_t>((size_t)((c->h + spb - 1) / spb), (size_t)c->sm_count * 8);
+  const size_t need = 5 * (data_b + nrm_b) + round256(max_blocks * sizeof(double)) + 256;
+  if (need > kStaticScratchBytes)
+    return fail(c, DWF_EINVAL,
+                "lattice too large for the static scratch: needs " + std::to_string(need) + " bytes, the array holds " +
+                    std::to_string(kStaticScratchBytes));
+  void *base = nullptr;
+  CK(static_scratch_address(c->device, &base));
+  unsigned char *cur = static_cast<unsigned char *>(base);
+  Field f[5];
+  for (auto &x : f) {
+    x.v = cur;
+    cur += data_b;
+    x.nrm = nrm_b ? reinterpret_cast<float *>(cur) : nullptr;
+    cur += nrm_b;
+  }
+  double *part = reinterpret_cast<double *>(cur);
+  cur += round256(max_blocks * sizeof(double));
+  unsigned *ticket = reinterpret_cast<unsigned *>(cur);
+
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  ReductionScratchSwap swap(c, part, ticket);
+  // the array keeps the previous call's contents: the ticket must start at zero
+  CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
+  CK(cudaMemsetAsync(d_out, 0, full, st));
+  const Geom g = geom(c);
+  const int cls = DWF_KC_OTHER;
+  Field &in = f[0], &out = f[1], &tA = f[2], &tB = f[3], &tC = f[4];
+  const int inpar = op == DWF_OP_DEO ? 1 : op == DWF_OP_DOE ? 0 : parity;
+  const int outpar = op == DWF_OP_DEO ? 0 : op == DWF_OP_DOE ? 1 : parity;
+  {
+    Timed t(c, st, cls);
+    CK(pack_any(prec, d_in, in, g, inpar, c->sm_count, st));
+  }
+  switch (op) {
+    case DWF_OP_DEO:
+    case DWF_OP_DOE: {
+      HopArgs a = hop_args(c, prec, outpar);
+      a.in = in;
+      a.out = out;
+      a.coef = -0.5;
+      TRY(hop(c, st, prec, E_PLAIN, a, cls));
+      break;
+    }
+    case DWF_OP_M5:
+    case DWF_OP_M5T:
+      TRY(smix(c, st, prec, S_PLAIN, in, out, op == DWF_OP_M5 ? MK_M5 : MK_M5T, 1.0, cls));
+      break;
+    case DWF_OP_C:
+      TRY(op_c(c, st, prec, parity, in, out, tA, cls));
+      break;
+    case DWF_OP_CDAG:
+      TRY(op_cdag(c, st, prec, parity, in, out, tA, tB, cls));
+      break;
+    case DWF_OP_CCDAG:
+      TRY(op_cdag(c, st, prec, parity, in, tC, tA, tB, cls));
+      TRY(op_c(c, st, prec, parity, tC, out, tA, cls));
+      break;
+  }
+  {
+    Timed t(c, st, cls);
+    CK(unpack_any(prec, out, d_out, g, outpar, c->sm_count, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return pull_scalars(c, st);
+}

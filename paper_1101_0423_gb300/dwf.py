@@ -80,6 +80,7 @@ def load(build_if_missing: bool = True):
         "dwf_load_gauge_dev": ([vp, vp, vp], i),
         "dwf_apply_eo": ([vp, i, i, i, dp, dp], i),
         "dwf_apply_eo_dev": ([vp, i, i, i, vp, vp, vp], i),
+        "dwf_apply_eo_dev_static": ([vp, i, i, i, vp, vp, vp], i),
         "dwf_solve": ([vp, dp, dp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats)], i),
         "dwf_solve_dev": ([vp, vp, vp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), vp], i),
         "dwf_last_error": ([vp], ctypes.c_char_p),
@@ -167,6 +168,12 @@ def dwf_apply_eo(ctx, op, prec, parity, x) -> np.ndarray:
 def dwf_apply_eo_dev(ctx, op, prec, parity, d_in, d_out, stream=None):
     _check(ctx, load().dwf_apply_eo_dev(ctx, int(op), int(prec), int(parity), _ptr(d_in), _ptr(d_out),
                                         _stream(stream)))
+
+
+def dwf_apply_eo_dev_static(ctx, op, prec, parity, d_in, d_out, stream=None):
+    """Allocation-free dwf_apply_eo_dev: work fields live in the library's static device array."""
+    _check(ctx, load().dwf_apply_eo_dev_static(ctx, int(op), int(prec), int(parity), _ptr(d_in), _ptr(d_out),
+                                               _stream(stream)))
 
 
 def _params(params=None, **kw) -> SolveParams:
