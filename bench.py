@@ -35,9 +35,10 @@ WORKLOAD = "dwf_full_solve_16x16x16x32_Ns16_cosine_mq0.02_tol1e-10"
 METRIC = "CG Gflops & % HBM roofline (16^3x32,Ns16); served solves/s, p99 latency"
 PAPER_BEST_GFLOPS = 233.0  # GTX 480, CG (mixed), same lattice (Table 1): other hardware, context
 
-# ncu DRAM traffic per launch of the dominant kernel class, from profiles/ (bytes), keyed by
-# the kernel class; filled from the committed ncu summary of the current kernel source.
-NCU_TRAFFIC = {}
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch, bytes, of the
+# FP32 kernel classes at this workload, from profiles/k_hop_f32_16x16x16x32_Ns16.md.  It is
+# valid only for the kernel source it was captured on; clear it when k_hop changes.
+NCU_TRAFFIC = {"hop_m5": 216.4e6, "hop_update": 735.1e6}
 
 
 def flops_ccdag(n, ns):

@@ -63,6 +63,9 @@ struct CGScalars {
   double target2;  // (tol |b|)^2
   double red;      // result slot of plain norm reductions
   double red2;
+  double alpha;     // (r, r) / (p, A p), set by the reduction that finishes |C^dag p|^2
+  float alpha_f;    // the same in FP32 for the FP32-arithmetic kernels
+  float beta_f;     // beta in FP32
   double rr_start;  // |r|^2 at the last restart (divergence guard)
   double rr_min;    // smallest |r|^2 since the last restart (stall guard)
   int restart_flag;  // set on device when an FP64 restart is due (a RS_* reason); kernels then skip work
@@ -175,6 +178,24 @@ __device__ __forceinline__ void store_sp(Field f, long cb, int s, int Ns,
   }
 }
 
+// one 16-byte chunk k of (cb, s) (FP64: 2 reals, FP32: 4 reals); unnormalised precisions only
+template <int P>
+__device__ __forceinline__ void load_chunk(const Field f, long cb, int s, int Ns, int k,
+                                           typename PT<P>::real (&o)[PT<P>::RPC]) {
+  static_assert(!PT<P>::HALF, "chunk access needs an unnormalised precision");
+  const typename PT<P>::chunk c = ((const typename PT<P>::chunk *)f.v)[((size_t)cb * PT<P>::NCH + k) * Ns + s];
+  if constexpr (P == P_F64) { o[0] = c.x; o[1] = c.y; }
+  else { o[0] = c.x; o[1] = c.y; o[2] = c.z; o[3] = c.w; }
+}
+template <int P>
+__device__ __forceinline__ void store_chunk(Field f, long cb, int s, int Ns, int k,
+                                            const typename PT<P>::real (&v)[PT<P>::RPC]) {
+  static_assert(!PT<P>::HALF, "chunk access needs an unnormalised precision");
+  typename PT<P>::chunk *b = (typename PT<P>::chunk *)f.v + ((size_t)cb * PT<P>::NCH + k) * Ns + s;
+  if constexpr (P == P_F64) *b = make_double2(v[0], v[1]);
+  else *b = make_float4(v[0], v[1], v[2], v[3]);
+}
+
 // ------------------------------------------------------------------ links
 
 template <int P>
@@ -223,35 +244,120 @@ __device__ __forceinline__ void phase(R &re, R &im) {
   else if constexpr (PH == 3) { R t = re; re = im; im = -t; }
 }
 
-// h_j = psi_j + S (A psi_dn)_j for the projected 2-spinor row j (colour a)
-template <int MU, int S, int J, typename R>
-__device__ __forceinline__ void project_row(R (&h)[2][3][2], const R (&ps)[24], int a) {
-  constexpr int src = 2 + a_col(MU, J);
-  R vr = ps[2 * (a + 3 * src)], vi = ps[2 * (a + 3 * src) + 1];
-  phase<a_ph(MU, J)>(vr, vi);
-  h[J][a][0] = ps[2 * (a + 3 * J)] + S * vr;
-  h[J][a][1] = ps[2 * (a + 3 * J) + 1] + S * vi;
+// ------------------------------------------------------------------ packed FP32 pairs
+//
+// Blackwell executes two FP32 operations per instruction on a 64-bit register pair
+// (add/sub/mul/fma .rn.f32x2).  A complex number (re, im) is such a pair, so a complex
+// multiply-accumulate w h + a costs two packed FMAs:  (wr, wr) h + (-wi, wi) (him, hre) + a.
+
+struct f2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f2 pk2(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(f2 x, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+// a * b + c
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ f2 swp2(f2 x) {
+  float a, b;
+  upk2(x, a, b);
+  return pk2(b, a);
 }
 
-// lower spin 2+K of (1 + S g_mu) applied to the upper result: S (A^dag wh)_K
-template <int MU, int S, int K, typename R>
-__device__ __forceinline__ void rebuild_row(R (&acc)[24], const R (&wh)[2][3][2], int a) {
-  R vr = wh[ad_col(MU, K)][a][0], vi = wh[ad_col(MU, K)][a][1];
-  phase<ad_ph(MU, K)>(vr, vi);
-  acc[2 * (a + 3 * (2 + K))] += S * vr;
-  acc[2 * (a + 3 * (2 + K)) + 1] += S * vi;
+// up + S * phase(PH) * z with the sign S a run-time value, given as the packed pairs
+// s2 = (S, S), ns2 = (-S, -S), sa = (-S, S), nsa = (S, -S)
+struct SignPairs {
+  f2 s2, ns2, sa, nsa;
+};
+__device__ __forceinline__ SignPairs sign_pairs(float S) {
+  return SignPairs{pk2(S, S), pk2(-S, -S), pk2(-S, S), pk2(S, -S)};
+}
+template <int PH>
+__device__ __forceinline__ f2 add_phase_rt(f2 up, f2 z, const SignPairs &sg) {
+  if constexpr (PH == 0) return fma2(z, sg.s2, up);
+  else if constexpr (PH == 2) return fma2(z, sg.ns2, up);
+  else if constexpr (PH == 1) return fma2(swp2(z), sg.sa, up);   // i z = (-zi, zr)
+  else return fma2(swp2(z), sg.nsa, up);                          // -i z = (zi, -zr)
 }
 
-// acc += (1 + S g_mu) W psi,  S = -1 (forward, 1 - g) or +1 (backward, 1 + g)
-template <int MU, int S, typename R>
-__device__ __forceinline__ void hop_dir(R (&acc)[24], const R (&ps)[24], const R (&W)[18]) {
+// acc += (1 + S g_mu) W psi with S = +-1 at run time (forward hops S = -1, backward S = +1),
+// so the two threads of a pair run the same instructions
+template <int MU>
+__device__ __forceinline__ void hop_dir_f2s(f2 (&acc)[12], const f2 (&ps)[12], const float4 *Wp,
+                                            const SignPairs &sg) {
+  f2 h[2][3], hs[2][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    h[0][a] = add_phase_rt<a_ph(MU, 0)>(ps[a], ps[a + 3 * (2 + a_col(MU, 0))], sg);
+    h[1][a] = add_phase_rt<a_ph(MU, 1)>(ps[a + 3], ps[a + 3 * (2 + a_col(MU, 1))], sg);
+    hs[0][a] = swp2(h[0][a]);
+    hs[1][a] = swp2(h[1][a]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float4 w0 = Wp[3 * a], w1 = Wp[3 * a + 1], w2 = Wp[3 * a + 2];
+    const f2 A0 = pk2(w0.x, w0.y), B0 = pk2(w0.z, w0.w);
+    const f2 A1 = pk2(w1.x, w1.y), B1 = pk2(w1.z, w1.w);
+    const f2 A2 = pk2(w2.x, w2.y), B2 = pk2(w2.z, w2.w);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      f2 wh = mul2(A0, h[j][0]);
+      wh = fma2(B0, hs[j][0], wh);
+      wh = fma2(A1, h[j][1], wh);
+      wh = fma2(B1, hs[j][1], wh);
+      wh = fma2(A2, h[j][2], wh);
+      wh = fma2(B2, hs[j][2], wh);
+      acc[a + 3 * j] = add2(acc[a + 3 * j], wh);
+      if (ad_col(MU, 0) == j) acc[a + 6] = add_phase_rt<ad_ph(MU, 0)>(acc[a + 6], wh, sg);
+      if (ad_col(MU, 1) == j) acc[a + 9] = add_phase_rt<ad_ph(MU, 1)>(acc[a + 9], wh, sg);
+    }
+  }
+}
+
+// FP64 version of hop_dir with the sign S at run time
+template <int MU, typename R>
+__device__ __forceinline__ void hop_dir_s(R (&acc)[24], const R (&ps)[24], const R (&W)[18], R S) {
   R h[2][3][2];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    project_row<MU, S, 0>(h, ps, a);
-    project_row<MU, S, 1>(h, ps, a);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int src = 2 + a_col(MU, j);
+      R vr = ps[2 * (a + 3 * src)], vi = ps[2 * (a + 3 * src) + 1];
+      switch (a_ph(MU, j)) {
+        case 1: { R t = vr; vr = -vi; vi = t; } break;
+        case 2: vr = -vr; vi = -vi; break;
+        case 3: { R t = vr; vr = vi; vi = -t; } break;
+        default: break;
+      }
+      h[j][a][0] = ps[2 * (a + 3 * j)] + S * vr;
+      h[j][a][1] = ps[2 * (a + 3 * j) + 1] + S * vi;
+    }
   }
-  R wh[2][3][2];
 #pragma unroll
   for (int j = 0; j < 2; ++j)
 #pragma unroll
@@ -263,19 +369,22 @@ __device__ __forceinline__ void hop_dir(R (&acc)[24], const R (&ps)[24], const R
         re += ur * h[j][b][0] - ui * h[j][b][1];
         im += ur * h[j][b][1] + ui * h[j][b][0];
       }
-      wh[j][a][0] = re;
-      wh[j][a][1] = im;
-    }
+      acc[2 * (a + 3 * j)] += re;
+      acc[2 * (a + 3 * j) + 1] += im;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      acc[2 * (a + 3 * j)] += wh[j][a][0];
-      acc[2 * (a + 3 * j) + 1] += wh[j][a][1];
+      for (int k = 0; k < 2; ++k) {
+        if (ad_col(MU, k) != j) continue;
+        R vr = re, vi = im;
+        switch (ad_ph(MU, k)) {
+          case 1: { R t = vr; vr = -vi; vi = t; } break;
+          case 2: vr = -vr; vi = -vi; break;
+          case 3: { R t = vr; vr = vi; vi = -t; } break;
+          default: break;
+        }
+        acc[2 * (a + 3 * (2 + k))] += S * vr;
+        acc[2 * (a + 3 * (2 + k)) + 1] += S * vi;
+      }
     }
-    rebuild_row<MU, S, 0>(acc, wh, a);
-    rebuild_row<MU, S, 1>(acc, wh, a);
-  }
 }
 
 }  // namespace dwf

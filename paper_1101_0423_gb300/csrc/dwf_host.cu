@@ -1261,7 +1261,7 @@ extern "C" dwf_status dwf_apply_eo_dev_static(dwf_ctx *c, int op, int prec, int 
   const size_t n = (size_t)c->h * c->Ns;
   const size_t data_b = round256(n * site_bytes(prec));
   const size_t nrm_b = prec >= P_F16 ? round256(n * sizeof(float)) : 0;
-  const long spb = sites_per_block(prec, c->Ns);
+  const long spb = std::min(hop_sites_per_block(prec, c->Ns), sites_per_block(prec, c->Ns));
   const size_t max_blocks = std::max<size_t>((size_t)((c->h + spb - 1) / spb), (size_t)c->sm_count * 8);
   const size_t need = 5 * (data_b + nrm_b) + round256(max_blocks * sizeof(double)) + 256;
   if (need > kStaticScratchBytes)

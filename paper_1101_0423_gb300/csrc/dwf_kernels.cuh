@@ -59,30 +59,39 @@ enum { ERR_TMA_TIMEOUT = 1 };
 
 // sum over the first `nact` lanes of a warp (lanes >= nact may not exist: the block size
 // need not be a multiple of 32); result valid in lane 0
-__device__ __forceinline__ double warp_sum(double v, int nact) {
-  const int lane = (threadIdx.x + threadIdx.y * blockDim.x) & 31;
+__device__ __forceinline__ int lin_tid() {
+  return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+}
+__device__ __forceinline__ int nthreads() { return blockDim.x * blockDim.y * blockDim.z; }
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v, int nact) {
+  const int lane = lin_tid() & 31;
   const unsigned mask = nact >= 32 ? 0xffffffffu : ((1u << nact) - 1u);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double t = __shfl_down_sync(mask, v, o);
+    const V t = __shfl_down_sync(mask, v, o);
     if (lane + o < nact) v += t;
   }
   return v;
 }
 
-// sum over the block (result valid in thread 0); `ws` holds >= 32 doubles
-__device__ __forceinline__ double block_sum(double v, double *ws) {
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-  const int nthr = blockDim.x * blockDim.y;
+// sum over the block (result valid in thread 0); `ws` holds >= 32 doubles.  The 32 lanes
+// of a warp are summed in the kernel's own precision V (FP32 kernels keep their FP32
+// pipes; GB300's FP64 units are few), the warp sums in FP64 and in a fixed order.
+template <typename V>
+__device__ __forceinline__ double block_sum(V v, double *ws) {
+  const int tid = lin_tid();
+  const int nthr = nthreads();
   const int nw = (nthr + 31) >> 5;
-  v = warp_sum(v, min(32, nthr - (tid & ~31)));
+  v = warp_sum<V>(v, min(32, nthr - (tid & ~31)));
   __syncthreads();
-  if ((tid & 31) == 0) ws[tid >> 5] = v;
+  if ((tid & 31) == 0) ws[tid >> 5] = (double)v;
   __syncthreads();
   double r = 0;
   if (tid < 32) {
     r = tid < nw ? ws[tid] : 0.0;
-    r = warp_sum(r, 32);
+    r = warp_sum<double>(r, 32);
   }
   return r;
 }
@@ -93,11 +102,17 @@ enum { FIN_NONE = 0, FIN_RED = 1, FIN_RED2 = 2, FIN_QQ = 3, FIN_CG = 4 };
 __device__ __forceinline__ void finish(int fin, double tot, CGScalars *sc) {
   if (fin == FIN_RED) sc->red = tot;
   else if (fin == FIN_RED2) sc->red2 = tot;
-  else if (fin == FIN_QQ) sc->qq = tot;
+  else if (fin == FIN_QQ) {
+    // Algorithm 1: alpha = (r, r) / (p, A p), with (p, A p) = |C^dag p|^2
+    sc->qq = tot;
+    sc->alpha = sc->rr / tot;
+    sc->alpha_f = (float)sc->alpha;
+  }
   else if (fin == FIN_CG) {
     // end of one CG iteration (Algorithm 1): beta = (r_new, r_new) / (r, r)
     const double rr_new = tot;
     sc->beta = rr_new / sc->rr;
+    sc->beta_f = (float)sc->beta;
     sc->rr_old = sc->rr;
     sc->rr = rr_new;
     sc->iter += 1;
@@ -118,13 +133,13 @@ __device__ __forceinline__ void finish(int fin, double tot, CGScalars *sc) {
 }
 
 // grid-wide deterministic sum; every thread of every block must call it
-__device__ __forceinline__ void grid_sum(double v, double *partials, unsigned *ticket, int fin,
-                                         CGScalars *sc) {
+template <typename V>
+__device__ __forceinline__ void grid_sum(V v, double *partials, unsigned *ticket, int fin, CGScalars *sc) {
   __shared__ double ws[32];
   __shared__ int am_last;
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-  const int nthr = blockDim.x * blockDim.y;
-  double bs = block_sum(v, ws);
+  const int tid = lin_tid();
+  const int nthr = nthreads();
+  double bs = block_sum<V>(v, ws);
   if (tid == 0) {
     partials[blockIdx.x] = bs;
     __threadfence();
@@ -136,7 +151,7 @@ __device__ __forceinline__ void grid_sum(double v, double *partials, unsigned *t
     __threadfence();
     double s = 0;
     for (unsigned i = tid; i < gridDim.x; i += nthr) s += __ldcg(partials + i);
-    double tot = block_sum(s, ws);
+    double tot = block_sum<double>(s, ws);
     if (tid == 0) {
       finish(fin, tot, sc);
       *ticket = 0u;
@@ -177,32 +192,57 @@ struct HopArgs {
   unsigned *ticket;
 };
 
-// dynamic shared memory layout of k_hop (bytes): [mbarrier 16][links][K][stage buffer]
-template <int P>
-__host__ __device__ inline size_t hop_link_bytes(int spb) {
-  return (size_t)spb * 8 * PT<P>::LREALS * sizeof(typename PT<P>::lreal);
-}
-template <int P>
-__host__ __device__ inline size_t hop_smem_bytes(int spb, int Ns, bool has_m) {
-  size_t b = 16 + ((hop_link_bytes<P>(spb) + 15) & ~size_t(15));
-  if (has_m) {
-    b += (size_t)2 * Ns * Ns * sizeof(typename PT<P>::real);
-    b = (b + 15) & ~size_t(15);
-    b += (size_t)spb * Ns * 24 * sizeof(typename PT<P>::real);
-  }
-  return b;
+// L2 prefetch of a contiguous range (an epilogue operand of this CTA's sites)
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-template <int P, int EPI>
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// dynamic shared memory of k_hop, in bytes:
+//   [mbarrier, 64 B][links as copied][neighbour indices][links packed for f32x2][stage][K]
+// FP32-arithmetic kernels (F32, fp16, bf16) expand each link once per CTA into nine
+// 16-byte entries (wr, wr, -wi, wi) -- the 16-bit forms rebuild their third row there --
+// and keep K duplicated as (k, k) pairs; FP64 kernels use the links as copied.
+template <int P> struct HopSmem {
+  static constexpr bool F2 = !(P == P_F64);
+  __host__ __device__ static size_t raw(int spb) { return (size_t)spb * 8 * PT<P>::LREALS * sizeof(typename PT<P>::lreal); }
+  __host__ __device__ static size_t off_raw() { return 64; }
+  __host__ __device__ static size_t off_nbr(int spb) { return off_raw() + align16(raw(spb)); }
+  __host__ __device__ static size_t off_pk(int spb) { return off_nbr(spb) + align16((size_t)spb * 8 * 4); }
+  __host__ __device__ static size_t end_pk(int spb) { return off_pk(spb) + (F2 ? (size_t)spb * 8 * 9 * 16 : 0); }
+  // the M5 staging buffer reuses the link area, which is dead once the hop sum is formed
+  __host__ __device__ static size_t off_stage(int) { return off_raw(); }
+  __host__ __device__ static size_t stage(int spb, int Ns) {
+    return (size_t)spb * (Ns * 24 * sizeof(typename PT<P>::real) + 16);
+  }
+  __host__ __device__ static size_t off_k(int spb, int Ns) {
+    const size_t a = end_pk(spb), b = off_stage(spb) + stage(spb, Ns);
+    return align16(a > b ? a : b);
+  }
+  __host__ __device__ static size_t bytes(int spb, int Ns, bool has_m) {
+    return off_k(spb, Ns) + (has_m ? align16((size_t)2 * Ns * Ns * (F2 ? 8 : sizeof(double))) : 0);
+  }
+};
+template <int P>
+__host__ __device__ inline size_t hop_smem_bytes(int spb, int Ns, bool has_m) {
+  return HopSmem<P>::bytes(spb, Ns, has_m);
+}
+
+// k_hop: one thread per (site, s), CTA = (Ns, spb).  Eight gathers of the neighbours'
+// spinors (Eq. 12), the hop sum in packed FP32 pairs (or FP64), then the epilogue.
+template <int P, int EPI, int NSC>
 __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
   using T = PT<P>;
   using R = typename T::real;
   using E = EpiT<EPI>;
-  extern __shared__ __align__(16) unsigned char sm[];
-  const int Ns = a.Ns;
+  using SM = HopSmem<P>;
+  constexpr bool F2 = SM::F2;
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int Ns = NSC ? NSC : a.Ns;
   const int s = threadIdx.x, sl = threadIdx.y, spb = blockDim.y;
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-  const int nthr = blockDim.x * blockDim.y;
+  const int tid = lin_tid();
+  const int nthr = nthreads();
   const long cb0 = (long)blockIdx.x * spb;
   const int nsite = (int)min((long)spb, a.h - cb0);
   const bool active = sl < nsite;
@@ -211,76 +251,168 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
   if (a.use_flag && a.sc->restart_flag) return;  // uniform over the grid
 
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
-  typename T::lreal *sL = reinterpret_cast<typename T::lreal *>(sm + 16);
-  R *sK = reinterpret_cast<R *>(sm + 16 + ((hop_link_bytes<P>(spb) + 15) & ~size_t(15)));
-  R *sB = reinterpret_cast<R *>(reinterpret_cast<unsigned char *>(sK) +
-                                (((size_t)2 * Ns * Ns * sizeof(R) + 15) & ~size_t(15)));
+  typename T::lreal *sL = reinterpret_cast<typename T::lreal *>(sm + SM::off_raw());
+  int *sN = reinterpret_cast<int *>(sm + SM::off_nbr(spb));
+  float4 *sP = reinterpret_cast<float4 *>(sm + SM::off_pk(spb));
+  unsigned char *sS = sm + SM::off_stage(spb);
+  unsigned char *sKb = sm + SM::off_k(spb, Ns);
 
-  // stage this CTA's links: one TMA bulk copy of nsite * 8 links (contiguous, 16-byte sized)
+  // the CTA's links arrive with one TMA bulk copy (nsite * 8 links, contiguous, 16-byte sized)
   if (tid == 0) mbar_init(bar, 1);
+  for (int i = tid; i < nsite * 8; i += nthr) sN[i] = __ldg(a.nbr + cb0 * 8 + i);
+  if constexpr (E::has_m) {
+    if constexpr (F2) {
+      const float *Kg = static_cast<const float *>(a.K);
+      float2 *sK2 = reinterpret_cast<float2 *>(sKb);
+      for (int i = tid; i < 2 * Ns * Ns; i += nthr) {
+        const float k = (float)a.coef * Kg[i];
+        sK2[i] = make_float2(k, k);
+      }
+    } else {
+      const double *Kg = static_cast<const double *>(a.K);
+      double *sKd = reinterpret_cast<double *>(sKb);
+      for (int i = tid; i < 2 * Ns * Ns; i += nthr) sKd[i] = a.coef * Kg[i];
+    }
+  }
   __syncthreads();
-  const uint32_t lbytes = (uint32_t)(nsite * 8 * T::LREALS * sizeof(typename T::lreal));
   if (tid == 0) {
+    const uint32_t lbytes = (uint32_t)SM::raw(nsite);
     mbar_expect_tx(bar, lbytes);
     bulk_g2s(sL, static_cast<const typename T::lreal *>(a.gauge) + (size_t)cb0 * 8 * T::LREALS, lbytes, bar);
+    const uint32_t ob = (uint32_t)((size_t)nsite * T::NCH * Ns * 16);
+    const size_t off = (size_t)cb0 * T::NCH * Ns * 16;
+    if constexpr (EPI == E_XPAY_G5 || EPI == E_XPAY || EPI == E_M_XPAY || EPI == E_CG_UPDATE || EPI == E_RESID)
+      prefetch_l2(static_cast<const unsigned char *>(a.y.v) + off, ob);
+    if constexpr (EPI == E_CG_UPDATE) {
+      prefetch_l2(static_cast<const unsigned char *>(a.r.v) + off, ob);
+      prefetch_l2(static_cast<const unsigned char *>(a.x.v) + off, ob);
+      prefetch_l2(static_cast<const unsigned char *>(a.p.v) + off, ob);
+    }
+    if constexpr (EPI == E_RESID) prefetch_l2(static_cast<const unsigned char *>(a.b.v) + off, ob);
   }
-  if constexpr (E::has_m) {
-    const R *Kg = static_cast<const R *>(a.K);
-    for (int i = tid; i < 2 * Ns * Ns; i += nthr) sK[i] = (R)a.coef * Kg[i];
+  // bounded wait, outcome agreed by the whole CTA before anyone acts on it
+  {
+    const bool ok = mbar_wait(bar, 0, kWaitTries);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(&a.sc->error, ERR_TMA_TIMEOUT);
+      mbar_wait(bar, 0, kWaitTries);  // give the copy in flight a bounded time to land
+      return;
+    }
   }
-  int nb[8];
-  if (active) {
+  if constexpr (F2) {
+    // expand every link once: nine (wr, wr, -wi, wi) entries; rebuild row 3 of 16-bit links
+    for (int l = tid; l < nsite * 8; l += nthr) {
+      float W[18];
+      load_link<P>(sL + (size_t)l * T::LREALS, W);
 #pragma unroll
-    for (int d = 0; d < 8; ++d) nb[d] = __ldg(a.nbr + cb * 8 + d);
+      for (int e = 0; e < 9; ++e) sP[(size_t)l * 9 + e] = make_float4(W[2 * e], W[2 * e], -W[2 * e + 1], W[2 * e + 1]);
+    }
+    __syncthreads();
   }
-  const bool ok = mbar_wait(bar, 0, kWaitTries);
-  if (!ok) {
-    if (tid == 0) atomicExch(&a.sc->error, ERR_TMA_TIMEOUT);
-    mbar_wait(bar, 0, kWaitTries);  // give an in-flight copy a bounded time to land
-    return;
-  }
-  if constexpr (E::has_m) __syncthreads();  // sK visible
 
   R acc[24];
-#pragma unroll
-  for (int c = 0; c < 24; ++c) acc[c] = 0;
   if (active) {
-    const typename T::lreal *myL = sL + (size_t)sl * 8 * T::LREALS;
-    R ps[24], W[18];
-    load_sp_ro<P>(a.in, nb[0], s, Ns, ps); load_link<P>(myL + 0 * T::LREALS, W); hop_dir<0, -1>(acc, ps, W);
-    load_sp_ro<P>(a.in, nb[1], s, Ns, ps); load_link<P>(myL + 1 * T::LREALS, W); hop_dir<1, -1>(acc, ps, W);
-    load_sp_ro<P>(a.in, nb[2], s, Ns, ps); load_link<P>(myL + 2 * T::LREALS, W); hop_dir<2, -1>(acc, ps, W);
-    load_sp_ro<P>(a.in, nb[3], s, Ns, ps); load_link<P>(myL + 3 * T::LREALS, W); hop_dir<3, -1>(acc, ps, W);
-    load_sp_ro<P>(a.in, nb[4], s, Ns, ps); load_link<P>(myL + 4 * T::LREALS, W); hop_dir<0, 1>(acc, ps, W);
-    load_sp_ro<P>(a.in, nb[5], s, Ns, ps); load_link<P>(myL + 5 * T::LREALS, W); hop_dir<1, 1>(acc, ps, W);
-    load_sp_ro<P>(a.in, nb[6], s, Ns, ps); load_link<P>(myL + 6 * T::LREALS, W); hop_dir<2, 1>(acc, ps, W);
-    load_sp_ro<P>(a.in, nb[7], s, Ns, ps); load_link<P>(myL + 7 * T::LREALS, W); hop_dir<3, 1>(acc, ps, W);
+    const int *nb = sN + sl * 8;
+    if constexpr (F2) {
+      f2 ac2[12];
+#pragma unroll
+      for (int q = 0; q < 12; ++q) ac2[q] = pk2(0.f, 0.f);
+      const SignPairs fw = sign_pairs(-1.f), bw = sign_pairs(1.f);
+      const float4 *myP = sP + (size_t)sl * 8 * 9;
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        float ps1[24];
+        load_sp_ro<P>(a.in, nb[d], s, Ns, ps1);
+        f2 ps[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) ps[q] = pk2(ps1[2 * q], ps1[2 * q + 1]);
+        switch (d) {  // forward hops (1 - g_mu), then backward hops (1 + g_mu)
+          case 0: hop_dir_f2s<0>(ac2, ps, myP, fw); break;
+          case 1: hop_dir_f2s<1>(ac2, ps, myP + 9, fw); break;
+          case 2: hop_dir_f2s<2>(ac2, ps, myP + 18, fw); break;
+          case 3: hop_dir_f2s<3>(ac2, ps, myP + 27, fw); break;
+          case 4: hop_dir_f2s<0>(ac2, ps, myP + 36, bw); break;
+          case 5: hop_dir_f2s<1>(ac2, ps, myP + 45, bw); break;
+          case 6: hop_dir_f2s<2>(ac2, ps, myP + 54, bw); break;
+          default: hop_dir_f2s<3>(ac2, ps, myP + 63, bw); break;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 12; ++q) upk2(ac2[q], acc[2 * q], acc[2 * q + 1]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 24; ++c) acc[c] = 0;
+      const typename T::lreal *myL = sL + (size_t)sl * 8 * T::LREALS;
+      R ps[24], W[18];
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        load_sp_ro<P>(a.in, nb[d], s, Ns, ps);
+        load_link<P>(myL + d * T::LREALS, W);
+        const R S = d < 4 ? (R)-1 : (R)1;
+        switch (d & 3) {
+          case 0: hop_dir_s<0>(acc, ps, W, S); break;
+          case 1: hop_dir_s<1>(acc, ps, W, S); break;
+          case 2: hop_dir_s<2>(acc, ps, W, S); break;
+          default: hop_dir_s<3>(acc, ps, W, S); break;
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 24; ++c) acc[c] = 0;
   }
 
   if constexpr (E::has_m) {
     // M5-type epilogue (Sec. 3.3): out_s = sum_t K_{st} H_t per chirality; the Ns slices
-    // of a site are in this CTA, staged through shared memory
-    R *mine = sB + ((size_t)sl * Ns + s) * 24;
+    // of a site are in this CTA, staged through shared memory (per-site stride padded by
+    // 16 bytes against bank conflicts; the stage reuses the link area)
+    R *sB = reinterpret_cast<R *>(sS);
+    const int sstride = Ns * 24 + 16 / (int)sizeof(R);
+    R *mine = sB + (size_t)sl * sstride + (size_t)s * 24;
+    __syncthreads();  // every warp is done with the links the stage overwrites
 #pragma unroll
     for (int c = 0; c < 24; ++c) mine[c] = acc[c];
     __syncthreads();
     if (active) {
-      const R *site = sB + (size_t)sl * Ns * 24;
+      const R *site = sB + (size_t)sl * sstride;
+      if constexpr (F2) {
+        const f2 *sK2 = reinterpret_cast<const f2 *>(sKb);
+        f2 o[12];
 #pragma unroll
-      for (int c = 0; c < 24; ++c) acc[c] = 0;
-      for (int t = 0; t < Ns; ++t) {
-        const R kp = sK[t * Ns + s];              // K+[s][t]
-        const R km = sK[Ns * Ns + t * Ns + s];    // K-[s][t]
-        const R *v = site + t * 24;
+        for (int q = 0; q < 12; ++q) o[q] = pk2(0.f, 0.f);
+#pragma unroll 4
+        for (int t = 0; t < Ns; ++t) {
+          const f2 kp = sK2[t * Ns + s];            // (K+[s][t], K+[s][t])
+          const f2 km = sK2[Ns * Ns + t * Ns + s];  // (K-[s][t], K-[s][t])
+          const float4 *v4 = reinterpret_cast<const float4 *>(site + t * 24);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) acc[c] += kp * v[c];
+          for (int k = 0; k < 6; ++k) {
+            const float4 v = v4[k];
+            const f2 kk = k < 3 ? kp : km;
+            o[2 * k] = fma2(kk, pk2(v.x, v.y), o[2 * k]);
+            o[2 * k + 1] = fma2(kk, pk2(v.z, v.w), o[2 * k + 1]);
+          }
+        }
 #pragma unroll
-        for (int c = 12; c < 24; ++c) acc[c] += km * v[c];
+        for (int q = 0; q < 12; ++q) upk2(o[q], acc[2 * q], acc[2 * q + 1]);
+      } else {
+        const double *sKd = reinterpret_cast<const double *>(sKb);
+#pragma unroll
+        for (int c = 0; c < 24; ++c) acc[c] = 0;
+        for (int t = 0; t < Ns; ++t) {
+          const R kp = sKd[t * Ns + s];
+          const R km = sKd[Ns * Ns + t * Ns + s];
+          const R *v = site + t * 24;
+#pragma unroll
+          for (int c = 0; c < 12; ++c) acc[c] += kp * v[c];
+#pragma unroll
+          for (int c = 12; c < 24; ++c) acc[c] += km * v[c];
+        }
       }
     }
   }
 
-  double part = 0;
+  R part = 0;
   if (active) {
     if constexpr (EPI == E_PLAIN) {
 #pragma unroll
@@ -292,15 +424,13 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
       R y[24];
       load_sp<P>(a.y, cb, s, Ns, y);
       const R cf = (R)a.coef;
-      R pr = 0;
 #pragma unroll
       for (int c = 0; c < 24; ++c) {
         const R g = (EPI == E_XPAY_G5 && c >= 12) ? -cf : cf;
         y[c] += g * acc[c];
-        pr += y[c] * y[c];
+        part += y[c] * y[c];
       }
       store_sp<P>(a.out, cb, s, Ns, y);
-      part = (double)pr;
     } else if constexpr (EPI == E_M_XPAY) {
       R y[24];
       load_sp<P>(a.y, cb, s, Ns, y);
@@ -308,39 +438,59 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
       for (int c = 0; c < 24; ++c) y[c] += acc[c];
       store_sp<P>(a.out, cb, s, Ns, y);
     } else if constexpr (EPI == E_CG_UPDATE) {
-      // Algorithm 1: alpha = (r, r) / (p, A p) with (p, A p) = |C^dag p|^2
-      const R alpha = (R)(a.sc->rr / a.sc->qq);
-      R y[24], r[24], xx[24], pp[24];
-      load_sp<P>(a.y, cb, s, Ns, y);
-      load_sp<P>(a.r, cb, s, Ns, r);
-      load_sp<P>(a.x, cb, s, Ns, xx);
-      load_sp<P>(a.p, cb, s, Ns, pp);
-      R pr = 0;
+      // alpha = (r, r) / (p, A p) was formed once by the reduction that produced (p, A p)
+      R alpha;
+      if constexpr (P == P_F64) alpha = a.sc->alpha;
+      else alpha = a.sc->alpha_f;
+      if constexpr (!T::HALF) {
+        // chunk by chunk: four operands of 16 bytes live at a time, not 4 x 24 reals
+        constexpr int RPC = T::RPC;
 #pragma unroll
-      for (int c = 0; c < 24; ++c) {
-        const R ap = y[c] + acc[c];
-        r[c] -= alpha * ap;
-        xx[c] += alpha * pp[c];
-        pr += r[c] * r[c];
+        for (int k = 0; k < T::NCH; ++k) {
+          R y[RPC], r[RPC], xx[RPC], pp[RPC];
+          load_chunk<P>(a.y, cb, s, Ns, k, y);
+          load_chunk<P>(a.r, cb, s, Ns, k, r);
+          load_chunk<P>(a.x, cb, s, Ns, k, xx);
+          load_chunk<P>(a.p, cb, s, Ns, k, pp);
+#pragma unroll
+          for (int j = 0; j < RPC; ++j) {
+            const R ap = y[j] + acc[k * RPC + j];
+            r[j] -= alpha * ap;
+            xx[j] += alpha * pp[j];
+            part += r[j] * r[j];
+          }
+          store_chunk<P>(a.r, cb, s, Ns, k, r);
+          store_chunk<P>(a.x, cb, s, Ns, k, xx);
+        }
+      } else {
+        R y[24], r[24], xx[24], pp[24];
+        load_sp<P>(a.y, cb, s, Ns, y);
+        load_sp<P>(a.r, cb, s, Ns, r);
+        load_sp<P>(a.x, cb, s, Ns, xx);
+        load_sp<P>(a.p, cb, s, Ns, pp);
+#pragma unroll
+        for (int c = 0; c < 24; ++c) {
+          const R ap = y[c] + acc[c];
+          r[c] -= alpha * ap;
+          xx[c] += alpha * pp[c];
+          part += r[c] * r[c];
+        }
+        store_sp<P>(a.r, cb, s, Ns, r);
+        store_sp<P>(a.x, cb, s, Ns, xx);
       }
-      store_sp<P>(a.r, cb, s, Ns, r);
-      store_sp<P>(a.x, cb, s, Ns, xx);
-      part = (double)pr;
     } else if constexpr (EPI == E_RESID) {
       R y[24], bb[24];
       load_sp<P>(a.y, cb, s, Ns, y);
       load_sp<P>(a.b, cb, s, Ns, bb);
-      R pr = 0;
 #pragma unroll
       for (int c = 0; c < 24; ++c) {
         bb[c] -= y[c] + acc[c];
-        pr += bb[c] * bb[c];
+        part += bb[c] * bb[c];
       }
       store_sp<P>(a.out, cb, s, Ns, bb);
-      part = (double)pr;
     }
   }
-  if constexpr (E::has_red) grid_sum(part, a.partials, a.ticket, a.fin, a.sc);
+  if constexpr (E::has_red) grid_sum<R>(part, a.partials, a.ticket, a.fin, a.sc);
 }
 
 // ------------------------------------------------------------------ s-mixing kernel
@@ -372,7 +522,7 @@ __host__ __device__ inline size_t smix_smem_bytes(int spb, int Ns, bool dual) {
 template <int P, int MODE>
 __global__ void __launch_bounds__(256) k_smix(const SmixArgs a) {
   using R = typename PT<P>::real;
-  extern __shared__ __align__(16) unsigned char sm[];
+  extern __shared__ __align__(128) unsigned char sm[];
   const int Ns = a.Ns;
   const int s = threadIdx.x, sl = threadIdx.y, spb = blockDim.y;
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
@@ -395,7 +545,9 @@ __global__ void __launch_bounds__(256) k_smix(const SmixArgs a) {
   if (active) {
     if constexpr (MODE == S_CGP) {
       R r[24];
-      const R beta = (R)a.sc->beta;
+      R beta;
+      if constexpr (P == P_F64) beta = a.sc->beta;
+      else beta = a.sc->beta_f;
       load_sp<P>(a.r, cb, s, Ns, r);
       load_sp<P>(a.p, cb, s, Ns, v);
 #pragma unroll

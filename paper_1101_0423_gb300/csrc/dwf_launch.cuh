@@ -7,9 +7,19 @@
 namespace dwf {
 
 // threads per CTA of the per-site kernels: the Ns slices of spb sites
+// (at most 64 sites, which bounds the shared memory of small-Ns CTAs)
 inline int sites_per_block(int P, int Ns) {
   const int target = (P == P_F64) ? 128 : 256;
   int spb = target / Ns;
+  if (spb > 64) spb = 64;
+  return spb < 1 ? 1 : spb;
+}
+
+// sites per CTA of k_hop, whose CTA is (Ns, spb)
+inline int hop_sites_per_block(int P, int Ns) {
+  const int target = (P == P_F64) ? 128 : 256;
+  int spb = target / Ns;
+  if (spb > 64) spb = 64;
   return spb < 1 ? 1 : spb;
 }
 
@@ -20,31 +30,49 @@ inline int vec_grid(long n, int sm_count) {
   return (int)(g < 1 ? 1 : g);
 }
 
-template <int P, int EPI>
+template <int P, int EPI, int NSC>
 cudaError_t hop_go(const HopArgs &a, cudaStream_t st) {
-  const int spb = sites_per_block(P, a.Ns);
+  const int spb = hop_sites_per_block(P, a.Ns);
   const size_t smem = hop_smem_bytes<P>(spb, a.Ns, EpiT<EPI>::has_m);
   static size_t configured = 0;
   if (smem > 48 * 1024 && configured < smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_hop<P, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_hop<P, EPI, NSC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
   const long nblk = (a.h + spb - 1) / spb;
-  k_hop<P, EPI><<<(unsigned)nblk, dim3(a.Ns, spb), smem, st>>>(a);
+  k_hop<P, EPI, NSC><<<(unsigned)nblk, dim3(a.Ns, spb), smem, st>>>(a);
   return cudaGetLastError();
+}
+
+// the inner-CG kernels get a compile-time Ns for the fifth-dimension extents in use
+template <int P, int EPI>
+cudaError_t hop_ns(const HopArgs &a, cudaStream_t st) {
+  if constexpr (P != P_F64 && (EPI == E_M || EPI == E_XPAY_G5 || EPI == E_CG_UPDATE)) {
+    switch (a.Ns) {
+      case 8: return hop_go<P, EPI, 8>(a, st);
+      case 12: return hop_go<P, EPI, 12>(a, st);
+      case 16: return hop_go<P, EPI, 16>(a, st);
+      case 20: return hop_go<P, EPI, 20>(a, st);
+      case 24: return hop_go<P, EPI, 24>(a, st);
+      case 32: return hop_go<P, EPI, 32>(a, st);
+      default: break;
+    }
+  }
+  return hop_go<P, EPI, 0>(a, st);
 }
 
 template <int P>
 cudaError_t hop_launch(int epi, const HopArgs &a, cudaStream_t st) {
   switch (epi) {
-    case E_PLAIN: return hop_go<P, E_PLAIN>(a, st);
-    case E_M: return hop_go<P, E_M>(a, st);
-    case E_XPAY_G5: return hop_go<P, E_XPAY_G5>(a, st);
-    case E_XPAY: return hop_go<P, E_XPAY>(a, st);
-    case E_M_XPAY: return hop_go<P, E_M_XPAY>(a, st);
-    case E_CG_UPDATE: return hop_go<P, E_CG_UPDATE>(a, st);
-    case E_RESID: return hop_go<P, E_RESID>(a, st);
+    case E_PLAIN: return hop_ns<P, E_PLAIN>(a, st);
+    case E_M: return hop_ns<P, E_M>(a, st);
+    case E_XPAY_G5: return hop_ns<P, E_XPAY_G5>(a, st);
+    case E_XPAY: return hop_ns<P, E_XPAY>(a, st);
+    case E_M_XPAY: return hop_ns<P, E_M_XPAY>(a, st);
+    case E_CG_UPDATE: return hop_ns<P, E_CG_UPDATE>(a, st);
+    case E_RESID: return hop_ns<P, E_RESID>(a, st);
   }
   return cudaErrorInvalidValue;
 }
