@@ -98,7 +98,7 @@ enum {
 typedef struct {
     double tol;        /* stop when |b - C C^dag x| <= tol |b| in FP64 (default 1e-10) */
     double delta;      /* reliable-update trigger: restart when |r| < delta * max|r| since the
-                          last restart; <= 0 selects the default of the inner precision */
+                          last restart; <= 0 selects the default, 0.01 */
     int max_iter;      /* cap on inner CG iterations (default 100000) */
     int inner_prec;    /* DWF_PREC_* of the inner CG (default DWF_PREC_F32) */
     int mode;          /* DWF_MODE_* (default DWF_MODE_AUTO) */

@@ -884,7 +884,7 @@ extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_s
   if (prm.mode < DWF_MODE_AUTO || prm.mode > DWF_MODE_DEFECT) return fail(c, DWF_EINVAL, "unknown mode");
   if (!(prm.tol > 0.0) || prm.max_iter < 1) return fail(c, DWF_EINVAL, "tol must be > 0 and max_iter >= 1");
   if (prm.check_every < 1) prm.check_every = 8;
-  const double delta = prm.delta > 0.0 ? prm.delta : (prm.inner_prec >= DWF_PREC_F16 ? 0.3 : 0.1);
+  const double delta = prm.delta > 0.0 ? prm.delta : 0.01;
   cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
   dwf_solve_stats local;
   dwf_solve_stats *S_out = stats ? stats : &local;

@@ -15,9 +15,11 @@ inline int sites_per_block(int P, int Ns) {
   return spb < 1 ? 1 : spb;
 }
 
-// sites per CTA of k_hop, whose CTA is (Ns, spb)
+// sites per CTA of k_hop, whose CTA is (Ns, spb): 128 threads measured best at Ns = 16
+// (94 us against 103 us with 256 and 139 us with 512 for the FP32 hop + M5)
 inline int hop_sites_per_block(int P, int Ns) {
-  const int target = (P == P_F64) ? 128 : 256;
+  const int target = 128;
+  (void)P;
   int spb = target / Ns;
   if (spb > 64) spb = 64;
   return spb < 1 ? 1 : spb;
