@@ -203,6 +203,70 @@ dwf_status dwf_solve(dwf_ctx *ctx, const double *rhs, double *sol, const dwf_sol
 dwf_status dwf_solve_dev(dwf_ctx *ctx, const double *d_rhs, double *d_sol,
                          const dwf_solve_params *params, dwf_solve_stats *stats, void *stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Serving: a request loop over many solves (not in the paper, which runs one solve at a
+ * time; it is the production form of the same Schur-complement CG).  The server keeps
+ * gauge ensembles resident on the device, queues requests first come first served,
+ * admits a request when a slot is free and its device-memory estimate fits the budget,
+ * and runs admitted solves concurrently, each on its own CUDA stream, so work of requests
+ * that arrive while others run overlaps on the GPU.  Every solve is deterministic (fixed
+ * reduction order), so its result does not depend on what else runs beside it.
+ * Uses the CUDA device current when dwf_server_create is called.
+ * --------------------------------------------------------------------------------------- */
+typedef struct dwf_server dwf_server;
+
+typedef struct {
+    double hbm_budget_gb;   /* device memory the server may hold for contexts and solver
+                               state, GiB (default 150) */
+    int max_inflight;       /* solves running at once (default 4) */
+    int reserved[7];
+} dwf_server_params;
+
+typedef struct {
+    int dims[4];            /* lattice of the request; must match its gauge ensemble */
+    int Ns;
+    double m0, mq;
+    const double *omega;    /* Ns weights, copied at submission */
+    const double *sigma;    /* Ns weights, copied at submission */
+    int gauge;              /* handle from dwf_server_add_gauge */
+    const double *rhs;      /* host right-hand side (full-lattice host layout), copied */
+    dwf_solve_params params;/* solver settings (tol, system, inner_prec, ...) */
+} dwf_request;
+
+typedef struct {
+    dwf_status status;      /* status of the solve */
+    dwf_solve_stats stats;
+    double queue_ms;        /* submission to start of the solve */
+    double latency_ms;      /* submission to completion */
+} dwf_result;
+
+typedef struct {
+    long long submitted, completed, in_flight, queued;
+    double p50_ms, p99_ms, mean_ms;  /* latency (submission to completion) of completed requests */
+    double solves_per_s;             /* completed / (last completion - first submission) */
+    double hbm_reserved_gb;          /* device-memory estimate of the admitted contexts */
+} dwf_server_stats;
+
+void dwf_server_params_default(dwf_server_params *p);
+/* Create a server (no device work until a request runs).  params may be NULL. */
+dwf_status dwf_server_create(const dwf_server_params *params, dwf_server **out);
+/* Finish the running solves, drop the queued ones and free everything (NULL accepted). */
+dwf_status dwf_server_destroy(dwf_server *srv);
+/* Copy a gauge field (host layout, 72 * V4 doubles) to the device as a resident ensemble;
+ * *handle receives its id. */
+dwf_status dwf_server_add_gauge(dwf_server *srv, const int dims[4], const double *U, int *handle);
+/* Queue one solve; *ticket identifies it.  The request's arrays are copied before the call
+ * returns.  DWF_EINVAL for malformed requests, DWF_ENOMEM if its memory estimate alone
+ * exceeds the budget. */
+dwf_status dwf_submit(dwf_server *srv, const dwf_request *req, uint64_t *ticket);
+/* DWF_EAGAIN while the solve is queued or running.  Once done: fills *result (if not NULL),
+ * copies the solution into psi_out (if not NULL; full-lattice host layout), releases the
+ * ticket and returns DWF_OK (the solve's own status is result->status).  DWF_EINVAL for an
+ * unknown ticket. */
+dwf_status dwf_poll(dwf_server *srv, uint64_t ticket, double *psi_out, dwf_result *result);
+/* Latency percentiles, throughput and occupancy of the server so far. */
+dwf_status dwf_server_get_stats(dwf_server *srv, dwf_server_stats *stats);
+
 /* Text of the last error on ctx ("" if none); valid until the next call on ctx. */
 const char *dwf_last_error(const dwf_ctx *ctx);
 /* Name of a status code. */

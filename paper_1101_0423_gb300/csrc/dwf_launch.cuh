@@ -2,6 +2,8 @@
 // precision in k_f64.cu / k_f32.cu / k_half.cu so the three compile in parallel.
 #pragma once
 
+#include <atomic>
+
 #include "dwf_kernels.cuh"
 
 namespace dwf {
@@ -36,12 +38,12 @@ template <int P, int EPI, int NSC>
 cudaError_t hop_go(const HopArgs &a, cudaStream_t st) {
   const int spb = hop_sites_per_block(P, a.Ns);
   const size_t smem = hop_smem_bytes<P>(spb, a.Ns, EpiT<EPI>::has_m);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && configured < smem) {
+  static std::atomic<size_t> configured{0};  // launches may come from several host threads
+  if (smem > 48 * 1024 && configured.load() < smem) {
     cudaError_t e =
         cudaFuncSetAttribute(k_hop<P, EPI, NSC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
+    configured.store(smem);
   }
   const long nblk = (a.h + spb - 1) / spb;
   k_hop<P, EPI, NSC><<<(unsigned)nblk, dim3(a.Ns, spb), smem, st>>>(a);
@@ -83,11 +85,11 @@ template <int P, int MODE>
 cudaError_t smix_go(const SmixArgs &a, cudaStream_t st) {
   const int spb = sites_per_block(P, a.Ns);
   const size_t smem = smix_smem_bytes<P>(spb, a.Ns, MODE == S_DUAL);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && configured < smem) {
+  static std::atomic<size_t> configured{0};
+  if (smem > 48 * 1024 && configured.load() < smem) {
     cudaError_t e = cudaFuncSetAttribute(k_smix<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
+    configured.store(smem);
   }
   const long nblk = (a.h + spb - 1) / spb;
   k_smix<P, MODE><<<(unsigned)nblk, dim3(a.Ns, spb), smem, st>>>(a);

@@ -57,6 +57,33 @@ class SolveStats(ctypes.Structure):
         return d
 
 
+class ServerParams(ctypes.Structure):
+    _fields_ = [("hbm_budget_gb", ctypes.c_double), ("max_inflight", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("Ns", ctypes.c_int), ("m0", ctypes.c_double),
+                ("mq", ctypes.c_double), ("omega", ctypes.POINTER(ctypes.c_double)),
+                ("sigma", ctypes.POINTER(ctypes.c_double)), ("gauge", ctypes.c_int),
+                ("rhs", ctypes.POINTER(ctypes.c_double)), ("params", SolveParams)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("stats", SolveStats), ("queue_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("in_flight", ctypes.c_longlong), ("queued", ctypes.c_longlong),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("solves_per_s", ctypes.c_double), ("hbm_reserved_gb", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -86,6 +113,13 @@ def load(build_if_missing: bool = True):
         "dwf_last_error": ([vp], ctypes.c_char_p),
         "dwf_status_string": ([i], ctypes.c_char_p),
         "dwf_solve_params_default": ([ctypes.POINTER(SolveParams)], None),
+        "dwf_server_params_default": ([ctypes.POINTER(ServerParams)], None),
+        "dwf_server_create": ([ctypes.POINTER(ServerParams), ctypes.POINTER(vp)], i),
+        "dwf_server_destroy": ([vp], i),
+        "dwf_server_add_gauge": ([vp, ip, dp, ip], i),
+        "dwf_submit": ([vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], i),
+        "dwf_poll": ([vp, ctypes.c_uint64, dp, ctypes.POINTER(Result)], i),
+        "dwf_server_get_stats": ([vp, ctypes.POINTER(ServerStats)], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -234,3 +268,71 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- serving
+
+def dwf_server_params_default() -> ServerParams:
+    p = ServerParams()
+    load().dwf_server_params_default(ctypes.byref(p))
+    return p
+
+
+def dwf_server_create(hbm_budget_gb=None, max_inflight=None):
+    p = dwf_server_params_default()
+    if hbm_budget_gb is not None:
+        p.hbm_budget_gb = float(hbm_budget_gb)
+    if max_inflight is not None:
+        p.max_inflight = int(max_inflight)
+    out = ctypes.c_void_p()
+    st = load().dwf_server_create(ctypes.byref(p), ctypes.byref(out))
+    if st != DWF_OK:
+        raise DwfError(st, "dwf_server_create")
+    return out.value
+
+
+def dwf_server_destroy(srv):
+    _check(None, load().dwf_server_destroy(srv))
+
+
+def dwf_server_add_gauge(srv, dims, U) -> int:
+    U = _f64(U)
+    h = ctypes.c_int(-1)
+    st = load().dwf_server_add_gauge(srv, (ctypes.c_int * 4)(*[int(v) for v in dims]), _dp(U), ctypes.byref(h))
+    if st != DWF_OK:
+        raise DwfError(st, "dwf_server_add_gauge")
+    return h.value
+
+
+def dwf_submit(srv, dims, Ns, m0, mq, omega, sigma, gauge, rhs, params=None, **kw) -> int:
+    """Queue one solve; returns its ticket.  Keyword arguments override params fields."""
+    omega, sigma, rhs = _f64(omega), _f64(sigma), _f64(rhs)
+    r = Request()
+    r.dims = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    r.Ns, r.m0, r.mq, r.gauge = int(Ns), float(m0), float(mq), int(gauge)
+    r.omega, r.sigma, r.rhs = _dp(omega), _dp(sigma), _dp(rhs)
+    r.params = _params(params, **kw)
+    t = ctypes.c_uint64(0)
+    st = load().dwf_submit(srv, ctypes.byref(r), ctypes.byref(t))
+    if st != DWF_OK:
+        raise DwfError(st, "dwf_submit")
+    return t.value
+
+
+def dwf_poll(srv, ticket, out=None):
+    """None while queued or running; else (solution or None, result dict)."""
+    res = Result()
+    ptr = _dp(out) if out is not None else None
+    st = load().dwf_poll(srv, ctypes.c_uint64(ticket), ptr, ctypes.byref(res))
+    if st == DWF_EAGAIN:
+        return None
+    if st != DWF_OK:
+        raise DwfError(st, "dwf_poll")
+    return out, {"status": res.status, "stats": res.stats.as_dict(), "queue_ms": res.queue_ms,
+                 "latency_ms": res.latency_ms}
+
+
+def dwf_server_get_stats(srv) -> dict:
+    s = ServerStats()
+    _check(None, load().dwf_server_get_stats(srv, ctypes.byref(s)))
+    return s.as_dict()
