@@ -164,6 +164,78 @@ def cpu_baseline_sample():
                       f"{dt:.1f} s; same flop count as the GPU's CG iterations"}
 
 
+# ---------------------------------------------------------------- served workload
+
+SERVE_LATTICES_FULL = [(8, 8, 8, 8), (12, 12, 12, 24), (16, 16, 16, 32), (24, 24, 24, 48)]
+SERVE_NS = [8, 16, 24, 32]
+SERVE_WEIGHTS = ["shamir", "borici", "cosine"]
+
+
+def serve_requests(n, lattices, seed=77):
+    """n requests drawn uniformly from lattice x Ns x mq ~ U[0.005, 0.1] x weight set."""
+    from paper_1101_0423_gb300 import inputs
+    u = inputs.uniforms(seed, inputs.TAG_MISC, 4 * n)
+    reqs = []
+    for i in range(n):
+        reqs.append(dict(dims=lattices[int(u[4 * i] * len(lattices))], Ns=SERVE_NS[int(u[4 * i + 1] * 4)],
+                         mq=0.005 + 0.095 * u[4 * i + 2], weights=SERVE_WEIGHTS[int(u[4 * i + 3] * 3)],
+                         rhs_seed=1000 + i))
+    return reqs
+
+
+def serve_run(reqs, lam, gauges_np, inner_prec, max_inflight=4, budget_gb=150.0, seed=78):
+    """Submit reqs at Poisson arrival rate lam (1/s), poll until all finish; server stats."""
+    import numpy as np
+    from paper_1101_0423_gb300 import dwf, inputs
+    srv = dwf.dwf_server_create(hbm_budget_gb=budget_gb, max_inflight=max_inflight)
+    try:
+        handles = {d: dwf.dwf_server_add_gauge(srv, d, U) for d, U in gauges_np.items()}
+        gaps = -np.log(1.0 - inputs.uniforms(seed, inputs.TAG_ARRIVALS, len(reqs))) / lam
+        rhs = [inputs.gaussian_source(r["dims"], r["Ns"], seed=r["rhs_seed"]) for r in reqs]
+        pending, statuses = [], []
+        t0 = time.perf_counter()
+        next_t = t0
+        for r, g, b in zip(reqs, gaps, rhs):
+            next_t += g
+            while time.perf_counter() < next_t:
+                time.sleep(min(0.002, max(0.0, next_t - time.perf_counter())))
+            om, sg = inputs.weights(r["weights"], r["Ns"])
+            pending.append(dwf.dwf_submit(srv, r["dims"], r["Ns"], M0, r["mq"], om, sg, handles[r["dims"]], b,
+                                          inner_prec=inner_prec, tol=1e-10))
+        while pending:
+            left = []
+            for t in pending:
+                res = dwf.dwf_poll(srv, t)
+                if res is None:
+                    left.append(t)
+                else:
+                    statuses.append(res[1]["status"])
+            pending = left
+            time.sleep(0.002)
+        st = dwf.dwf_server_get_stats(srv)
+        st["ok"] = sum(1 for x in statuses if x == dwf.DWF_OK)
+        return st
+    finally:
+        dwf.dwf_server_destroy(srv)
+
+
+def serve_measure(n, lattices, inner_prec, fractions):
+    """Capacity from the requests solved one after another, then Poisson runs at each fraction."""
+    from paper_1101_0423_gb300 import inputs
+    reqs = serve_requests(n, lattices)
+    gauges_np = {d: inputs.gauge_field(d, EPS, seed=10 + i) for i, d in enumerate(SERVE_LATTICES_FULL)
+                 if d in {r["dims"] for r in reqs}}
+    seq = serve_run(reqs, 1e9, gauges_np, inner_prec, max_inflight=1)   # back to back, one at a time
+    capacity = seq["solves_per_s"]
+    out = []
+    for f in fractions:
+        st = serve_run(reqs, f * capacity, gauges_np, inner_prec)
+        out.append({"lambda_fraction": f, "lambda_per_s": f * capacity, "capacity_per_s": capacity,
+                    "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                    "mean_ms": st["mean_ms"], "completed": st["completed"], "ok": st["ok"]})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -172,9 +244,21 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--inner", default="f32", choices=["f32", "f16", "bf16", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="only the served sweep: 40 requests over all four lattices at 0.2..0.95 of capacity")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        from paper_1101_0423_gb300 import build as _b, dwf
+        _b.build()
+        for row in serve_measure(40, SERVE_LATTICES_FULL, dwf.PREC_BF16, [0.2, 0.4, 0.6, 0.8, 0.95]):
+            print(json.dumps({"metric": "served solves/s, p99 latency", "config": {
+                "workload": "served: uniform lattice {8^4,12^3x24,16^3x32,24^3x48} x Ns {8,16,24,32} x "
+                            "mq U[0.005,0.1] x {shamir,borici,cosine}, bf16 inner, tol 1e-10, 150 GB budget"},
+                **row}))
+        return
 
     import numpy as np
     import torch
@@ -318,6 +402,16 @@ def main():
         "clocks": clocks,
         "vs_baseline_note": "value / 233 Gflops (paper Table 1, GTX 480, same lattice): other hardware, context",
     }
+    if world == 1 and not args.no_serve:
+        # bounded served sample: 12 Poisson-arriving requests at 0.8 of the measured capacity,
+        # lattices up to 16^3x32 (the full sweep over all four lattices is `bench.py --serve`)
+        row = serve_measure(12, SERVE_LATTICES_FULL[:3], dwf.PREC_BF16, [0.8])[0]
+        out["served"] = {"solves_per_s": row["solves_per_s"], "p50_ms": row["p50_ms"], "p99_ms": row["p99_ms"],
+                         "lambda_per_s": row["lambda_per_s"], "capacity_per_s": row["capacity_per_s"],
+                         "requests": row["completed"], "ok": row["ok"],
+                         "sample": "12 requests, uniform lattice {8^4,12^3x24,16^3x32} x Ns {8,16,24,32} x "
+                                   "mq U[0.005,0.1] x {shamir,borici,cosine}, bf16 inner, tol 1e-10, "
+                                   "Poisson arrivals at 0.8 x single-stream capacity, 4 slots, 150 GB budget"}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_sample()
     print(json.dumps(out))

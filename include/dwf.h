@@ -84,7 +84,8 @@ enum {
 
 /* restart policy of the mixed-precision CG (Sec. 2.3) */
 enum {
-    DWF_MODE_AUTO = 0,     /* reliable updates; switch to defect correction if they stop converging */
+    DWF_MODE_AUTO = 0,     /* reliable updates; switch to defect correction if they stop converging,
+                              and from 16-bit to FP32 inner iterations if defect correction stops too */
     DWF_MODE_RELIABLE = 1, /* keep p across restarts (reliable updates) */
     DWF_MODE_DEFECT = 2    /* reset p := r at every restart (defect correction, Algorithm 2) */
 };
@@ -136,7 +137,9 @@ typedef struct {
     int class_launches[DWF_KC_COUNT];
     long long kernel_launches;       /* kernels this call launched (graph nodes included) */
     double bytes_hop_m5;             /* algorithmic bytes of one DWF_KC_HOP_M5 launch */
-    double reserved[3];
+    int inner_prec_used;             /* DWF_PREC_* of the inner CG at the end */
+    int escalations;                 /* AUTO mode: 16-bit inner CG replaced by FP32 (0 or 1) */
+    double reserved[2];
 } dwf_solve_stats;
 
 /* Fill p with the defaults listed above. */

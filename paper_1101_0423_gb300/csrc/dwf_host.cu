@@ -962,7 +962,7 @@ extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_s
 
   int iters = 0, restarts = 0, mode_now = prm.mode == DWF_MODE_DEFECT ? DWF_MODE_DEFECT : DWF_MODE_RELIABLE;
   double rhat2 = bnorm2, prev_rhat2 = bnorm2, rr_last = 0.0;
-  int switches = 0;
+  int switches = 0, escalations = 0;
   const int stall_iters = prm.stall_iters > 0 ? prm.stall_iters : 500;
   bool converged = bnorm2 == 0.0;
   dwf_status result = DWF_OK;
@@ -1060,6 +1060,30 @@ extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_s
       if (prm.mode == DWF_MODE_AUTO && mode_now == DWF_MODE_RELIABLE && failed) {
         mode_now = DWF_MODE_DEFECT;
         ++switches;
+      } else if (prm.mode == DWF_MODE_AUTO && mode_now == DWF_MODE_DEFECT && failed && S.prec >= P_F16) {
+        // 16-bit storage is too coarse for this system: continue from x_hat with FP32 inner
+        // iterations (the FP64 state x_hat, r_hat is untouched)
+        TRY(ensure_gauge(c, P_F32, st));
+        S.prec = P_F32;
+        TRY(get_buf(c, "cg_x", S.prec, &S.x));
+        TRY(get_buf(c, "cg_r", S.prec, &S.r));
+        TRY(get_buf(c, "cg_p", S.prec, &S.p));
+        TRY(get_buf(c, "cg_q", S.prec, &S.q));
+        TRY(get_buf(c, "cg_w", S.prec, &S.w));
+        TRY(get_buf(c, "cg_t", S.prec, &S.t));
+        TRY(get_buf(c, "cg_u", S.prec, &S.u));
+        CK(cudaMemsetAsync(S.x.v, 0, (size_t)c->h * c->Ns * site_bytes(S.prec), st));
+        CK(cudaMemsetAsync(S.p.v, 0, (size_t)c->h * c->Ns * site_bytes(S.prec), st));
+        TRY(convert(c, st, P_F64, S.rh, S.prec, S.r, DWF_KC_F64));
+        TRY(norm2(c, st, S.prec, S.r, FIN_RED2));
+        TRY(pull_scalars(c, st));
+        rr_last = c->h_sc->red2;
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+        first_batch = true;
+        ++escalations;
       }
       prev_rhat2 = rhat2;
       TRY(arm(tol_now, false, mode_now == DWF_MODE_DEFECT || failed, rr_last));
@@ -1158,6 +1182,8 @@ extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_s
                       (full ? flops_prep_recon(c->Ns) : 0.0));
   S_out->time_ms = ms;
   S_out->bytes_hop_m5 = n * (2.0 * site_bytes(S.prec) + 8.0 * link_bytes_per_site(S.prec) / 8.0 / c->Ns);
+  S_out->inner_prec_used = S.prec;
+  S_out->escalations = escalations;
   end_profile(c, S_out);
   S_out->kernel_launches = c->launches - launches0;
   if (result == DWF_OK && !converged) result = fail(c, DWF_ENOCONV, "not converged");

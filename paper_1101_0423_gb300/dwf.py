@@ -48,7 +48,8 @@ class SolveStats(ctypes.Structure):
                 ("true_res_full", ctypes.c_double), ("flops", ctypes.c_double),
                 ("time_ms", ctypes.c_double), ("class_ms", ctypes.c_double * 6),
                 ("class_launches", ctypes.c_int * 6), ("kernel_launches", ctypes.c_longlong),
-                ("bytes_hop_m5", ctypes.c_double), ("reserved", ctypes.c_double * 3)]
+                ("bytes_hop_m5", ctypes.c_double), ("inner_prec_used", ctypes.c_int),
+                ("escalations", ctypes.c_int), ("reserved", ctypes.c_double * 2)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("class_ms", "class_launches", "reserved")}

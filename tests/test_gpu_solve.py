@@ -114,3 +114,17 @@ def test_full_size_config1_solve(gpu_lib):
         psi, st = dwf.dwf_solve(ctx.h, eta, tol=1e-10)
     res = np.linalg.norm(eta - oracle.dfull(dims, ns, U, M0, mq, om, sg, psi)) / np.linalg.norm(eta)
     assert res <= 1e-10, f"oracle true residual {res:.3e}, stats {st}"
+
+
+def test_bf16_inner_escalates_to_fp32_when_defect_correction_stalls(gpu_lib):
+    """16^3 x 32 x Ns=16 Borici, mq = 0.0064: bf16 inner iterations cannot contract at this
+    conditioning; AUTO mode must finish with FP32 inner iterations and meet the residual."""
+    from paper_1101_0423_gb300 import dwf
+    dims, ns, mq = (16, 16, 16, 32), 16, 0.0064
+    om, sg = inputs.weights("borici", ns)
+    U = inputs.gauge_field(dims, 0.5, seed=12)
+    eta = inputs.gaussian_source(dims, ns, seed=1002)
+    with dwf.Context(dims, ns, M0, mq, om, sg, U) as ctx:
+        psi, st = dwf.dwf_solve(ctx.h, eta, inner_prec=dwf.PREC_BF16, tol=1e-10)
+    assert st["converged"] == 1 and st["true_res_full"] <= 1e-10
+    assert st["escalations"] == 1 and st["inner_prec_used"] == dwf.PREC_F32
