@@ -106,6 +106,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_over_ranks(ms, flops, device=None):
+    """Whole-job numbers of independent replicas: the slowest rank's time and the sum of the
+    work of all ranks (no data-path collective; only these two scalars are reduced)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return ms, flops
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    f = torch.tensor([float(flops)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    tdist.all_reduce(f, op=tdist.ReduceOp.SUM)
+    return float(t.item()), float(f.item())
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -316,15 +330,7 @@ def main():
     ms = e0.elapsed_time(e1)
     flops = sum(s["flops"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
-    t_max = ms
-    flops_all = flops
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        t_max = float(t.item())
-        f = torch.tensor([flops], device="cuda", dtype=torch.float64)
-        tdist.all_reduce(f)
-        flops_all = float(f.item())
+    t_max, flops_all = aggregate_over_ranks(ms, flops, device="cuda")
     value = flops_all / (t_max * 1e-3) / 1e9
 
     # ---- e2e: through dwf_solve with pinned host buffers, copies inside the timed region
@@ -347,11 +353,7 @@ def main():
         e2e_flops += st.flops
     barrier()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-        e2e_flops *= world
+    e2e_s, e2e_flops = aggregate_over_ranks(e2e_s, e2e_flops, device="cuda")
     e2e_value = e2e_flops / e2e_s / 1e9
     nbytes = eta.nbytes
 
