@@ -172,6 +172,34 @@ dwf_status dwf_apply_eo(dwf_ctx *ctx, int op, int prec, int parity, const double
 dwf_status dwf_apply_eo_dev(dwf_ctx *ctx, int op, int prec, int parity, const double *d_in,
                             double *d_out, void *stream);
 
+/* Solve nrhs systems with the same operator together (e.g. the 12 spin-colour point
+ * sources of a propagator, Sec. 2.2's valence use).  rhs and sol hold nrhs arrays of the
+ * dwf_solve layout one after another; stats, if not NULL, receives nrhs entries.  Every
+ * right-hand side has its own CG scalars, restarts and convergence (Algorithm 1-2, Sec. 2.3);
+ * all of them advance in the same kernel launches (one grid row per right-hand side) and the
+ * same CUDA graph.  A full-system batch aims its Schur residual at tol/4 (no second pass);
+ * the 16-bit-to-FP32 escalation of AUTO mode applies to single solves only.  Returns the
+ * first failure among the right-hand sides (DWF_ENOCONV if any did not converge). */
+dwf_status dwf_solve_batch(dwf_ctx *ctx, int nrhs, const double *rhs, double *sol,
+                           const dwf_solve_params *params, dwf_solve_stats *stats);
+/* Same with caller-owned device arrays, ordered on `stream`. */
+dwf_status dwf_solve_batch_dev(dwf_ctx *ctx, int nrhs, const double *d_rhs, double *d_sol,
+                               const dwf_solve_params *params, dwf_solve_stats *stats, void *stream);
+
+/* Quark propagator from the point x0 (the valence use of Sec. 2.2): the 12 spin-colour
+ * point sources are solved in one batch (dwf_solve_batch, DWF_SYS_FULL) and the 4D quark
+ * field is read off the two walls.  Conventions (the paper fixes none): source (beta, b)
+ * carries a 1 in spin beta, colour b at x0 on the s-slice of its chirality's wall -- s = 0
+ * for P+ (spins 0,1), s = Ns-1 for P- (spins 2,3) -- and q(x) = P- psi(x, 0) + P+ psi(x, Ns-1)
+ * (L moves P+ components up and P- components down in s, Eq. 3-4).
+ * prop receives V4 * 144 complex numbers, prop[site][alpha][a][beta][b] = q_{alpha a}(site)
+ * of source (beta, b), re/im interleaved.  stats, if not NULL, receives 12 entries. */
+dwf_status dwf_propagator(dwf_ctx *ctx, const int x0[4], const dwf_solve_params *params, double *prop,
+                          dwf_solve_stats *stats);
+/* Same with a caller-owned device output, ordered on `stream`. */
+dwf_status dwf_propagator_dev(dwf_ctx *ctx, const int x0[4], const dwf_solve_params *params, double *d_prop,
+                              dwf_solve_stats *stats, void *stream);
+
 /* Allocation-free variant of dwf_apply_eo_dev (the paper has no counterpart: it is a
  * service for callers that must not allocate device memory while they run -- code
  * recording a CUDA stream capture, where cudaMalloc is not allowed; applications whose

@@ -624,6 +624,7 @@ dwf_status dwf_destroy(dwf_ctx *c) {
   if (c->d_U) cudaFree(c->d_U);
   if (c->d_sc) cudaFree(c->d_sc);
   if (c->h_sc) cudaFreeHost(c->h_sc);
+  if (c->h_scb) cudaFreeHost(c->h_scb);
   if (c->d_part) cudaFree(c->d_part);
   if (c->d_ticket) cudaFree(c->d_ticket);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -768,24 +769,142 @@ dwf_status dwf_apply_eo(dwf_ctx *c, int op, int prec, int parity, const double *
 namespace {
 
 struct SolveState {
-  int prec, sp, op;
-  Field b, xh, rh, w64, t64, q64, u64;  // FP64, Schur parity (t64, u64: other parity)
-  Field x, r, p, q, w, t, u;            // inner precision
+  int prec, sp, op, K;
+  Field b, xh, rh;            // FP64 on the Schur parity, one field per right-hand side
+  Field w64, t64, q64, u64;   // FP64 temporaries of the restart operator (t64, u64: other parity)
+  Field x, r, p, q, w, t, u;  // inner precision, one field per right-hand side (t, u: other parity)
 };
 
-// one inner CG iteration on A = C C^dag (Algorithm 1), five kernels:
+size_t field_bytes(const dwf_ctx *c, int prec) { return (size_t)c->h * c->Ns * site_bytes(prec); }
+
+// field k of a batch of fields
+Field at(const dwf_ctx *c, Field f, int k, int prec) {
+  Field g = f;
+  if (g.v) g.v = static_cast<char *>(g.v) + (size_t)k * field_bytes(c, prec);
+  if (g.nrm) g.nrm += (size_t)k * c->h * c->Ns;
+  return g;
+}
+
+// K consecutive fields under one name (reallocated when a larger batch needs more)
+dwf_status get_buf_k(dwf_ctx *c, const std::string &name, int prec, int K, Field *f) {
+  if (K == 1) return get_buf(c, name, prec, f);
+  const size_t n = (size_t)c->h * c->Ns * K;
+  const size_t bytes = n * site_bytes(prec);
+  Buf &b = c->bufs["batch:" + name + "#" + std::to_string(prec)];
+  if (b.v && b.bytes < bytes) {
+    cudaFree(b.v);
+    if (b.nrm) cudaFree(b.nrm);
+    b.v = nullptr;
+    b.nrm = nullptr;
+  }
+  if (!b.v) {
+    CK(cudaMalloc(&b.v, bytes));
+    b.bytes = bytes;
+    if (prec >= P_F16) CK(cudaMalloc((void **)&b.nrm, n * sizeof(float)));
+    CK(cudaMemsetAsync(b.v, 0, bytes, c->stream));
+    if (b.nrm) CK(cudaMemsetAsync(b.nrm, 0, n * sizeof(float), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  f->v = b.v;
+  f->nrm = b.nrm;
+  return DWF_OK;
+}
+
+// scalars, partial sums and tickets of a batch (slot k at base + k)
+struct Slots {
+  CGScalars *d_sc, *h_sc;
+  double *d_part;
+  unsigned *d_ticket;
+};
+
+dwf_status batch_slots(dwf_ctx *c, int K, Slots *sl) {
+  if (K == 1) {
+    *sl = Slots{c->d_sc, c->h_sc, c->d_part, c->d_ticket};
+    return DWF_OK;
+  }
+  void *p;
+  TRY(get_raw(c, "batch_sc", K * sizeof(CGScalars), &p));
+  sl->d_sc = static_cast<CGScalars *>(p);
+  TRY(get_raw(c, "batch_part", (size_t)K * c->part_len * sizeof(double), &p));
+  sl->d_part = static_cast<double *>(p);
+  TRY(get_raw(c, "batch_ticket", K * sizeof(unsigned), &p));
+  sl->d_ticket = static_cast<unsigned *>(p);
+  if (c->h_scb_cap < K) {
+    if (c->h_scb) cudaFreeHost(c->h_scb);
+    c->h_scb = nullptr;
+    CK(cudaMallocHost((void **)&c->h_scb, K * sizeof(CGScalars)));
+    c->h_scb_cap = K;
+  }
+  sl->h_sc = c->h_scb;
+  memset(sl->h_sc, 0, K * sizeof(CGScalars));
+  CK(cudaMemsetAsync(sl->d_ticket, 0, K * sizeof(unsigned), c->stream));
+  CK(cudaMemcpyAsync(sl->d_sc, sl->h_sc, K * sizeof(CGScalars), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return DWF_OK;
+}
+
+// points the context's scalar/partials/ticket at one slot (or at the batch base) for a scope
+struct UseSlot {
+  dwf_ctx *c;
+  CGScalars *dsc, *hsc;
+  double *part;
+  unsigned *tick;
+  UseSlot(dwf_ctx *c_, const Slots &sl, int k)
+      : c(c_), dsc(c_->d_sc), hsc(c_->h_sc), part(c_->d_part), tick(c_->d_ticket) {
+    c->d_sc = sl.d_sc + k;
+    c->h_sc = sl.h_sc + k;
+    c->d_part = sl.d_part + (size_t)k * c->part_len;
+    c->d_ticket = sl.d_ticket + k;
+  }
+  ~UseSlot() {
+    c->d_sc = dsc;
+    c->h_sc = hsc;
+    c->d_part = part;
+    c->d_ticket = tick;
+  }
+};
+
+// one inner CG iteration on A = C C^dag (Algorithm 1) for every right-hand side, five kernels:
 //   p = r + beta p, w = M5^T g5 p | t = -1/2 M5^T H w | q = p + 1/2 g5 H t, |q|^2
 //   u = -1/2 M5 H q | Ap = q + 1/2 M5 H u, r -= alpha Ap, x += alpha p, |r|^2, beta
-dwf_status cg_iteration(dwf_ctx *c, cudaStream_t st, const SolveState &S) {
+dwf_status cg_iteration(dwf_ctx *c, cudaStream_t st, const SolveState &S, const Slots &sl) {
   const int P = S.prec;
-  TRY(smix(c, st, P, S_CGP, Field{nullptr, nullptr}, S.w, MK_M5T, 1.0, DWF_KC_SMIX_P, Field{nullptr, nullptr},
-           MK_ID, S.r, S.p, 1));
+  const size_t fs = field_bytes(c, P), ns = (size_t)c->h * c->Ns;
+  auto batch = [&](HopArgs &a) {
+    a.nrhs = S.K;
+    a.fstride = fs;
+    a.nstride = ns;
+    a.part_stride = c->part_len;
+    a.sc = sl.d_sc;
+    a.partials = sl.d_part;
+    a.ticket = sl.d_ticket;
+  };
+  {
+    SmixArgs m;
+    memset(&m, 0, sizeof(m));
+    m.out = S.w;
+    m.r = S.r;
+    m.p = S.p;
+    m.K = dmat(c, P, MK_M5T);
+    m.K2 = dmat(c, P, MK_ID);
+    m.coef = 1.0;
+    m.h = c->h;
+    m.Ns = c->Ns;
+    m.use_flag = 1;
+    m.sc = sl.d_sc;
+    m.nrhs = S.K;
+    m.fstride = fs;
+    m.nstride = ns;
+    Timed t(c, st, DWF_KC_SMIX_P);
+    CK(smix_any(P, S_CGP, m, st));
+  }
   HopArgs a = hop_args(c, P, S.op);
   a.in = S.w;
   a.out = S.t;
   a.K = dmat(c, P, MK_M5T);
   a.coef = -0.5;
   a.use_flag = 1;
+  batch(a);
   TRY(hop(c, st, P, E_M, a, DWF_KC_HOP_M5));
   HopArgs b = hop_args(c, P, S.sp);
   b.in = S.t;
@@ -794,6 +913,7 @@ dwf_status cg_iteration(dwf_ctx *c, cudaStream_t st, const SolveState &S) {
   b.coef = 0.5;
   b.fin = FIN_QQ;
   b.use_flag = 1;
+  batch(b);
   TRY(hop(c, st, P, E_XPAY_G5, b, DWF_KC_HOP_XPAY));
   HopArgs d = hop_args(c, P, S.op);
   d.in = S.q;
@@ -801,6 +921,7 @@ dwf_status cg_iteration(dwf_ctx *c, cudaStream_t st, const SolveState &S) {
   d.K = dmat(c, P, MK_M5);
   d.coef = -0.5;
   d.use_flag = 1;
+  batch(d);
   TRY(hop(c, st, P, E_M, d, DWF_KC_HOP_M5));
   HopArgs e = hop_args(c, P, S.sp);
   e.in = S.u;
@@ -812,24 +933,28 @@ dwf_status cg_iteration(dwf_ctx *c, cudaStream_t st, const SolveState &S) {
   e.coef = 0.5;
   e.fin = FIN_CG;
   e.use_flag = 1;
+  batch(e);
   TRY(hop(c, st, P, E_CG_UPDATE, e, DWF_KC_HOP_UPDATE));
   return DWF_OK;
 }
 
-// FP64 restart (Algorithm 2): x_hat += x, x = 0, r_hat = b - C C^dag x_hat, |r_hat|^2 -> red,
-// r = r_hat in the inner precision, |r|^2 -> red2
-dwf_status fp64_restart(dwf_ctx *c, cudaStream_t st, const SolveState &S) {
+// FP64 restart of right-hand side k (Algorithm 2), with the context pointed at its slot:
+// x_hat += x, x = 0, r_hat = b - C C^dag x_hat, |r_hat|^2 -> red, r = r_hat in the inner
+// precision, |r|^2 -> red2
+dwf_status fp64_restart(dwf_ctx *c, cudaStream_t st, const SolveState &S, int k) {
+  const Field xh = at(c, S.xh, k, P_F64), rh = at(c, S.rh, k, P_F64), bk = at(c, S.b, k, P_F64);
+  const Field x = at(c, S.x, k, S.prec), r = at(c, S.r, k, S.prec);
   {
     VecArgs v;
     memset(&v, 0, sizeof(v));
-    v.a = S.xh;
-    v.b = S.x;
+    v.a = xh;
+    v.b = x;
     v.n = c->h * c->Ns;
     v.Ns = c->Ns;
     Timed t(c, st, DWF_KC_F64);
     CK(accum_any(S.prec, v, c->sm_count, st));
   }
-  TRY(smix(c, st, P_F64, S_G5, S.xh, S.w64, MK_M5T, 1.0, DWF_KC_F64));
+  TRY(smix(c, st, P_F64, S_G5, xh, S.w64, MK_M5T, 1.0, DWF_KC_F64));
   HopArgs a = hop_args(c, P_F64, S.op);
   a.in = S.w64;
   a.out = S.t64;
@@ -838,7 +963,7 @@ dwf_status fp64_restart(dwf_ctx *c, cudaStream_t st, const SolveState &S) {
   TRY(hop(c, st, P_F64, E_M, a, DWF_KC_F64));
   HopArgs b = hop_args(c, P_F64, S.sp);
   b.in = S.t64;
-  b.y = S.xh;
+  b.y = xh;
   b.out = S.q64;
   b.coef = 0.5;
   b.fin = FIN_NONE;
@@ -852,14 +977,14 @@ dwf_status fp64_restart(dwf_ctx *c, cudaStream_t st, const SolveState &S) {
   HopArgs e = hop_args(c, P_F64, S.sp);
   e.in = S.u64;
   e.y = S.q64;
-  e.b = S.b;
-  e.out = S.rh;
+  e.b = bk;
+  e.out = rh;
   e.K = dmat(c, P_F64, MK_M5);
   e.coef = 0.5;
   e.fin = FIN_RED;
   TRY(hop(c, st, P_F64, E_RESID, e, DWF_KC_F64));
-  TRY(convert(c, st, P_F64, S.rh, S.prec, S.r, DWF_KC_F64));
-  TRY(norm2(c, st, S.prec, S.r, FIN_RED2));
+  TRY(convert(c, st, P_F64, rh, S.prec, r, DWF_KC_F64));
+  TRY(norm2(c, st, S.prec, r, FIN_RED2));
   return DWF_OK;
 }
 
@@ -868,32 +993,29 @@ double flops_cg_iter(int Ns) { return 5472.0 + 192.0 * Ns; }
 double flops_restart(int Ns) { return 5328.0 + 192.0 * Ns; }
 double flops_prep_recon(int Ns) { return 5160.0 + 384.0 * Ns; }
 
-}  // namespace
+constexpr int RS_DONE = 6;  // restart flag of a right-hand side that is finished
 
-extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_sol, const dwf_solve_params *pp,
-                                    dwf_solve_stats *stats, void *stream) {
-  TRY(check_ctx(c));
-  dwf_solve_params prm;
-  if (pp) prm = *pp;
-  else dwf_solve_params_default(&prm);
-  if (!d_rhs || !d_sol || !aligned16(d_rhs) || !aligned16(d_sol))
-    return fail(c, DWF_EINVAL, "null or non-16-byte-aligned field pointer");
-  if (!valid_prec(prm.inner_prec)) return fail(c, DWF_EINVAL, "unknown inner precision");
-  if (prm.system != DWF_SYS_FULL && prm.system != DWF_SYS_NORMAL) return fail(c, DWF_EINVAL, "unknown system");
-  if (prm.schur_parity != 0 && prm.schur_parity != 1) return fail(c, DWF_EINVAL, "schur_parity must be 0 or 1");
-  if (prm.mode < DWF_MODE_AUTO || prm.mode > DWF_MODE_DEFECT) return fail(c, DWF_EINVAL, "unknown mode");
-  if (!(prm.tol > 0.0) || prm.max_iter < 1) return fail(c, DWF_EINVAL, "tol must be > 0 and max_iter >= 1");
-  if (prm.check_every < 1) prm.check_every = 8;
+// per right-hand-side bookkeeping of the host loop
+struct RhsState {
+  double bnorm2 = 0, rhat2 = 0, prev_rhat2 = 0, rr_last = 0, res_full = 0;
+  int restarts = 0, iters = 0, mode = DWF_MODE_RELIABLE;
+  bool done = false, converged = false;
+  dwf_status status = DWF_OK;
+};
+
+// Solve K systems with the same operator; rhs/sol hold K full-lattice arrays one after another.
+dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf_solve_params prm,
+                      dwf_solve_stats *S_out, cudaStream_t st) {
   const double delta = prm.delta > 0.0 ? prm.delta : 0.01;
-  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
-  dwf_solve_stats local;
-  dwf_solve_stats *S_out = stats ? stats : &local;
-  memset(S_out, 0, sizeof(*S_out));
+  const bool full = prm.system == DWF_SYS_FULL;
+  const int stall_iters = prm.stall_iters > 0 ? prm.stall_iters : 500;
+  const char *trace_env = getenv("DWF_TRACE");
+  const bool trace = trace_env && trace_env[0] == '1';
+  for (int k = 0; k < K; ++k) memset(&S_out[k], 0, sizeof(dwf_solve_stats));
   begin_profile(c, prm.profile != 0);
   const long long launches0 = c->launches;
   TRY(ensure_gauge(c, P_F64, st));
   TRY(ensure_gauge(c, prm.inner_prec, st));
-
   cudaEvent_t ev0 = next_event(c), ev1 = next_event(c);
   CK(cudaEventRecord(ev0, st));
 
@@ -901,124 +1023,155 @@ extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_s
   S.prec = prm.inner_prec;
   S.sp = prm.schur_parity;
   S.op = 1 - S.sp;
-  TRY(get_buf(c, "b", P_F64, &S.b));
-  TRY(get_buf(c, "xh", P_F64, &S.xh));
-  TRY(get_buf(c, "rh", P_F64, &S.rh));
+  S.K = K;
+  TRY(get_buf_k(c, "b", P_F64, K, &S.b));
+  TRY(get_buf_k(c, "xh", P_F64, K, &S.xh));
+  TRY(get_buf_k(c, "rh", P_F64, K, &S.rh));
   TRY(get_buf(c, "w64", P_F64, &S.w64));
   TRY(get_buf(c, "t64", P_F64, &S.t64));
   TRY(get_buf(c, "q64", P_F64, &S.q64));
   TRY(get_buf(c, "u64", P_F64, &S.u64));
-  TRY(get_buf(c, "cg_x", S.prec, &S.x));
-  TRY(get_buf(c, "cg_r", S.prec, &S.r));
-  TRY(get_buf(c, "cg_p", S.prec, &S.p));
-  TRY(get_buf(c, "cg_q", S.prec, &S.q));
-  TRY(get_buf(c, "cg_w", S.prec, &S.w));
-  TRY(get_buf(c, "cg_t", S.prec, &S.t));
-  TRY(get_buf(c, "cg_u", S.prec, &S.u));
-  const Geom g = geom(c);
-  const bool full = prm.system == DWF_SYS_FULL;
-  Field eta[2], etap[2];
-  const size_t nbytes64 = (size_t)c->h * c->Ns * 192;
-
-  // ---- source: b on the Schur parity (Eq. 10 for the full system)
-  if (full) {
+  auto inner_bufs = [&]() -> dwf_status {
+    TRY(get_buf_k(c, "cg_x", S.prec, K, &S.x));
+    TRY(get_buf_k(c, "cg_r", S.prec, K, &S.r));
+    TRY(get_buf_k(c, "cg_p", S.prec, K, &S.p));
+    TRY(get_buf_k(c, "cg_q", S.prec, K, &S.q));
+    TRY(get_buf_k(c, "cg_w", S.prec, K, &S.w));
+    TRY(get_buf_k(c, "cg_t", S.prec, K, &S.t));
+    TRY(get_buf_k(c, "cg_u", S.prec, K, &S.u));
+    return DWF_OK;
+  };
+  TRY(inner_bufs());
+  Field eta[2], etap[2], phi[2], psi[2], dpsi[2];
+  if (full)
     for (int p = 0; p < 2; ++p) {
       TRY(get_buf(c, "eta" + std::to_string(p), P_F64, &eta[p]));
       TRY(get_buf(c, "etap" + std::to_string(p), P_F64, &etap[p]));
+      TRY(get_buf(c, "phi" + std::to_string(p), P_F64, &phi[p]));
+      TRY(get_buf(c, "psi" + std::to_string(p), P_F64, &psi[p]));
+      TRY(get_buf(c, "dpsi" + std::to_string(p), P_F64, &dpsi[p]));
+    }
+  Slots sl;
+  TRY(batch_slots(c, K, &sl));
+  const Geom g = geom(c);
+  const size_t full_doubles = (size_t)c->V4 * c->Ns * 24;
+  const size_t nbytes64 = field_bytes(c, P_F64);
+  // the full-system residual runs a little above the Schur one (by at most cond(S1)): the
+  // Schur system of a full solve aims at half the tolerance (a quarter in batches, which
+  // have no second pass)
+  const double tol_schur = full ? (K == 1 ? 0.5 : 0.25) * prm.tol : prm.tol;
+  std::vector<RhsState> R(K);
+  int escalations = 0;
+
+  // eta'_k = S1 eta_k on both parities (the shared temporaries eta, etap)
+  auto prep_eta = [&](int k) -> dwf_status {
+    for (int p = 0; p < 2; ++p) {
       {
         Timed t(c, st, DWF_KC_F64);
-        CK(pack_any(P_F64, d_rhs, eta[p], g, p, c->sm_count, st));
+        CK(pack_any(P_F64, d_rhs + (size_t)k * full_doubles, eta[p], g, p, c->sm_count, st));
       }
-      // eta' = S1 eta
       TRY(smix(c, st, P_F64, S_PLAIN, eta[p], etap[p], MK_S1, 1.0, DWF_KC_F64));
     }
-    // b = eta'_sp - M5 D^{sp,op} eta'_op = eta'_sp + 1/2 M5 H eta'_op
-    HopArgs a = hop_args(c, P_F64, S.sp);
-    a.in = etap[S.op];
-    a.y = etap[S.sp];
-    a.out = S.b;
-    a.K = dmat(c, P_F64, MK_M5);
-    a.coef = 0.5;
-    TRY(hop(c, st, P_F64, E_M_XPAY, a, DWF_KC_F64));
-  } else {
-    Timed t(c, st, DWF_KC_F64);
-    CK(pack_any(P_F64, d_rhs, S.b, g, S.sp, c->sm_count, st));
-  }
-  TRY(norm2(c, st, P_F64, S.b, FIN_RED));
-  // x_hat = 0, r_hat = b, r = b (inner precision), x = 0, p = 0
-  CK(cudaMemsetAsync(S.xh.v, 0, nbytes64, st));
-  CK(cudaMemcpyAsync(S.rh.v, S.b.v, nbytes64, cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemsetAsync(S.x.v, 0, (size_t)c->h * c->Ns * site_bytes(S.prec), st));
-  CK(cudaMemsetAsync(S.p.v, 0, (size_t)c->h * c->Ns * site_bytes(S.prec), st));
-  if (S.x.nrm) {
-    CK(cudaMemsetAsync(S.x.nrm, 0, (size_t)c->h * c->Ns * sizeof(float), st));
-    CK(cudaMemsetAsync(S.p.nrm, 0, (size_t)c->h * c->Ns * sizeof(float), st));
-  }
-  TRY(convert(c, st, P_F64, S.b, S.prec, S.r, DWF_KC_OTHER));
-  TRY(norm2(c, st, S.prec, S.r, FIN_RED2));
-  TRY(pull_scalars(c, st));
-  const double bnorm2 = c->h_sc->red;
-  const double tol2 = prm.tol * prm.tol;
+    return DWF_OK;
+  };
 
-  int iters = 0, restarts = 0, mode_now = prm.mode == DWF_MODE_DEFECT ? DWF_MODE_DEFECT : DWF_MODE_RELIABLE;
-  double rhat2 = bnorm2, prev_rhat2 = bnorm2, rr_last = 0.0;
-  int switches = 0, escalations = 0;
-  const int stall_iters = prm.stall_iters > 0 ? prm.stall_iters : 500;
-  bool converged = bnorm2 == 0.0;
-  dwf_status result = DWF_OK;
-  // (re)arm the inner CG after a restart: r already holds r_hat in the inner precision and
-  // red2 = |r|^2.  Reliable updates keep p (beta from the recomputed residual), defect
-  // correction restarts from p = r (beta = 0).
-  auto arm = [&](double tol_now, bool first, bool reset_p, double rr_conv) -> dwf_status {
+  // (re)arm the inner CG of right-hand side k after a restart: r_k holds r_hat in the inner
+  // precision with |r|^2 = rr_conv.  Reliable updates keep p (beta from the recomputed
+  // residual), defect correction restarts from p = r (beta = 0).
+  auto arm = [&](int k, double tol_now, bool first, bool reset_p, double rr_conv) -> dwf_status {
+    UseSlot use(c, sl, k);
     CGScalars &h = *c->h_sc;
     if (first) {
       h.rr_old = rr_conv;
       h.qq = 1.0;
-      h.beta = 0.0;
       h.iter = 0;
       h.iter_cap = prm.max_iter;
       h.error = 0;
       h.delta2 = delta * delta;
+      h.beta = 0.0;
     } else {
       h.beta = reset_p ? 0.0 : rr_conv / h.rr_old;
     }
+    h.beta_f = (float)h.beta;
     h.rr = rr_conv;
     h.rmax2 = rr_conv;
     h.rr_start = rr_conv;
     h.rr_min = rr_conv;
     h.iter_min = h.iter;
     h.stall_iters = stall_iters;
-    h.target2 = tol_now * tol_now * bnorm2;
-    h.restart_flag = 0;
+    h.target2 = tol_now * tol_now * R[k].bnorm2;
+    h.restart_flag = R[k].done ? RS_DONE : 0;
     return push_scalars(c, st);
   };
+
+  // ---- source: b_k on the Schur parity (Eq. 10 for the full system); x_hat = 0, r_hat = b,
+  // r = b in the inner precision, x = p = 0
+  CK(cudaMemsetAsync(S.x.v, 0, (size_t)K * field_bytes(c, S.prec), st));
+  CK(cudaMemsetAsync(S.p.v, 0, (size_t)K * field_bytes(c, S.prec), st));
+  if (S.x.nrm) {
+    CK(cudaMemsetAsync(S.x.nrm, 0, (size_t)K * c->h * c->Ns * sizeof(float), st));
+    CK(cudaMemsetAsync(S.p.nrm, 0, (size_t)K * c->h * c->Ns * sizeof(float), st));
+  }
+  CK(cudaMemsetAsync(S.xh.v, 0, (size_t)K * nbytes64, st));
+  for (int k = 0; k < K; ++k) {
+    UseSlot use(c, sl, k);
+    const Field bk = at(c, S.b, k, P_F64);
+    if (full) {
+      TRY(prep_eta(k));
+      // b = eta'_sp - M5 D^{sp,op} eta'_op = eta'_sp + 1/2 M5 H eta'_op
+      HopArgs a = hop_args(c, P_F64, S.sp);
+      a.in = etap[S.op];
+      a.y = etap[S.sp];
+      a.out = bk;
+      a.K = dmat(c, P_F64, MK_M5);
+      a.coef = 0.5;
+      TRY(hop(c, st, P_F64, E_M_XPAY, a, DWF_KC_F64));
+    } else {
+      Timed t(c, st, DWF_KC_F64);
+      CK(pack_any(P_F64, d_rhs + (size_t)k * full_doubles, bk, g, S.sp, c->sm_count, st));
+    }
+    TRY(norm2(c, st, P_F64, bk, FIN_RED));
+    CK(cudaMemcpyAsync(at(c, S.rh, k, P_F64).v, bk.v, nbytes64, cudaMemcpyDeviceToDevice, st));
+    TRY(convert(c, st, P_F64, bk, S.prec, at(c, S.r, k, S.prec), DWF_KC_OTHER));
+    TRY(norm2(c, st, S.prec, at(c, S.r, k, S.prec), FIN_RED2));
+    TRY(pull_scalars(c, st));
+    R[k].bnorm2 = R[k].rhat2 = R[k].prev_rhat2 = c->h_sc->red;
+    R[k].rr_last = c->h_sc->red2;
+    R[k].mode = prm.mode == DWF_MODE_DEFECT ? DWF_MODE_DEFECT : DWF_MODE_RELIABLE;
+    R[k].done = R[k].converged = R[k].bnorm2 == 0.0;
+  }
+  for (int k = 0; k < K; ++k) TRY(arm(k, tol_schur, true, true, R[k].rr_last));
+
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   struct GraphGuard {
     cudaGraphExec_t &e;
-    cudaGraph_t &g;
+    cudaGraph_t &gr;
     ~GraphGuard() {
       if (e) cudaGraphExecDestroy(e);
-      if (g) cudaGraphDestroy(g);
+      if (gr) cudaGraphDestroy(gr);
     }
   } graph_guard{gexec, graph};
   const bool use_graph = prm.use_graph && !c->profiling;
-  // DWF_TRACE=1 prints one line per FP64 restart to stderr
-  const char *trace_env = getenv("DWF_TRACE");
-  const bool trace = trace_env && trace_env[0] == '1';
   bool first_batch = true;
-  // mixed-precision CG until |b - A x_hat| <= tol_now |b| (FP64)
+  auto all_done = [&]() {
+    for (auto &x : R)
+      if (!x.done) return false;
+    return true;
+  };
+
+  // ---- mixed-precision CG until every |b_k - A x_hat_k| <= tol_now |b_k| (FP64)
   auto cg_loop = [&](double tol_now) -> dwf_status {
     const double tol2 = tol_now * tol_now;
-    converged = rhat2 <= tol2 * bnorm2;
-    while (!converged) {
-      // ---- one batch of inner iterations (the device skips the rest once a restart is due)
+    while (!all_done()) {
+      // one batch of inner iterations (the device skips a right-hand side once its restart
+      // is due or it is finished)
       if (use_graph && !first_batch) {
         if (!gexec) {
           CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
           const long long l0 = c->launches;
-          for (int k = 0; k < prm.check_every; ++k) {
-            dwf_status s2 = cg_iteration(c, st, S);
+          for (int it = 0; it < prm.check_every; ++it) {
+            dwf_status s2 = cg_iteration(c, st, S, sl);
             if (s2 != DWF_OK) {
               cudaStreamEndCapture(st, &graph);
               return s2;
@@ -1031,75 +1184,79 @@ extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_s
         CK(cudaGraphLaunch(gexec, st));
         c->launches += 5LL * prm.check_every;
       } else {
-        for (int k = 0; k < prm.check_every; ++k) TRY(cg_iteration(c, st, S));
+        for (int it = 0; it < prm.check_every; ++it) TRY(cg_iteration(c, st, S, sl));
       }
       first_batch = false;
-      TRY(pull_scalars(c, st));
-      const int reason = c->h_sc->restart_flag;
-      if (!reason) continue;
-      iters = c->h_sc->iter;
-      // ---- reliable update / defect correction restart in FP64
-      TRY(fp64_restart(c, st, S));
-      TRY(pull_scalars(c, st));
-      ++restarts;
-      rhat2 = c->h_sc->red;
-      rr_last = c->h_sc->red2;
-      if (trace)
-        fprintf(stderr, "dwf: restart %d iter %d reason %d |r_iter|/|b| %.3e |r_true|/|b| %.3e mode %s\n", restarts,
-                iters, reason, sqrt(c->h_sc->rr / bnorm2), sqrt(rhat2 / bnorm2),
-                mode_now == DWF_MODE_DEFECT ? "defect" : "reliable");
-      if (!std::isfinite(rhat2)) return fail(c, DWF_ENOCONV, "residual is not finite");
-      if (rhat2 <= tol2 * bnorm2) {
-        converged = true;
-        break;
-      }
-      if (iters >= prm.max_iter) return fail(c, DWF_ENOCONV, "max_iter reached");
-      // Sec. 2.3: fall back to defect correction when the reliable updates stop converging
-      // (the true residual grew, or the inner recursion diverged or stalled)
-      const bool failed = rhat2 > prev_rhat2 || reason == RS_DIVERGED || reason == RS_STALLED;
-      if (prm.mode == DWF_MODE_AUTO && mode_now == DWF_MODE_RELIABLE && failed) {
-        mode_now = DWF_MODE_DEFECT;
-        ++switches;
-      } else if (prm.mode == DWF_MODE_AUTO && mode_now == DWF_MODE_DEFECT && failed && S.prec >= P_F16) {
-        // 16-bit storage is too coarse for this system: continue from x_hat with FP32 inner
-        // iterations (the FP64 state x_hat, r_hat is untouched)
-        TRY(ensure_gauge(c, P_F32, st));
-        S.prec = P_F32;
-        TRY(get_buf(c, "cg_x", S.prec, &S.x));
-        TRY(get_buf(c, "cg_r", S.prec, &S.r));
-        TRY(get_buf(c, "cg_p", S.prec, &S.p));
-        TRY(get_buf(c, "cg_q", S.prec, &S.q));
-        TRY(get_buf(c, "cg_w", S.prec, &S.w));
-        TRY(get_buf(c, "cg_t", S.prec, &S.t));
-        TRY(get_buf(c, "cg_u", S.prec, &S.u));
-        CK(cudaMemsetAsync(S.x.v, 0, (size_t)c->h * c->Ns * site_bytes(S.prec), st));
-        CK(cudaMemsetAsync(S.p.v, 0, (size_t)c->h * c->Ns * site_bytes(S.prec), st));
-        TRY(convert(c, st, P_F64, S.rh, S.prec, S.r, DWF_KC_F64));
-        TRY(norm2(c, st, S.prec, S.r, FIN_RED2));
+      CK(cudaMemcpyAsync(sl.h_sc, sl.d_sc, K * sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int k = 0; k < K; ++k) {
+        if (R[k].done) continue;
+        UseSlot use(c, sl, k);
+        if (c->h_sc->error) TRY(pull_scalars(c, st));  // reports DWF_ETIMEOUT and resets
+        const int reason = c->h_sc->restart_flag;
+        if (!reason) continue;
+        R[k].iters = c->h_sc->iter;
+        // ---- reliable update / defect correction restart in FP64
+        TRY(fp64_restart(c, st, S, k));
         TRY(pull_scalars(c, st));
-        rr_last = c->h_sc->red2;
-        if (gexec) cudaGraphExecDestroy(gexec);
-        if (graph) cudaGraphDestroy(graph);
-        gexec = nullptr;
-        graph = nullptr;
-        first_batch = true;
-        ++escalations;
+        ++R[k].restarts;
+        R[k].rhat2 = c->h_sc->red;
+        R[k].rr_last = c->h_sc->red2;
+        if (trace)
+          fprintf(stderr, "dwf: rhs %d restart %d iter %d reason %d |r_iter|/|b| %.3e |r_true|/|b| %.3e mode %s\n", k,
+                  R[k].restarts, R[k].iters, reason, sqrt(c->h_sc->rr / R[k].bnorm2), sqrt(R[k].rhat2 / R[k].bnorm2),
+                  R[k].mode == DWF_MODE_DEFECT ? "defect" : "reliable");
+        if (!std::isfinite(R[k].rhat2)) {
+          R[k].done = true;
+          R[k].status = fail(c, DWF_ENOCONV, "residual is not finite");
+        } else if (R[k].rhat2 <= tol2 * R[k].bnorm2) {
+          R[k].done = R[k].converged = true;
+        } else if (R[k].iters >= prm.max_iter) {
+          R[k].done = true;
+          R[k].status = fail(c, DWF_ENOCONV, "max_iter reached");
+        }
+        if (R[k].done) {
+          TRY(arm(k, tol_now, false, true, R[k].rr_last));  // parks the right-hand side
+          continue;
+        }
+        // Sec. 2.3: fall back to defect correction when the reliable updates stop converging
+        // (the true residual grew, or the inner recursion diverged or stalled)
+        const bool failed = R[k].rhat2 > R[k].prev_rhat2 || reason == RS_DIVERGED || reason == RS_STALLED;
+        if (prm.mode == DWF_MODE_AUTO && R[k].mode == DWF_MODE_RELIABLE && failed) {
+          R[k].mode = DWF_MODE_DEFECT;
+        } else if (prm.mode == DWF_MODE_AUTO && R[k].mode == DWF_MODE_DEFECT && failed && S.prec >= P_F16 &&
+                   K == 1) {
+          // 16-bit storage is too coarse for this system: continue from x_hat with FP32
+          // inner iterations (the FP64 state x_hat, r_hat is untouched)
+          TRY(ensure_gauge(c, P_F32, st));
+          S.prec = P_F32;
+          TRY(inner_bufs());
+          CK(cudaMemsetAsync(S.x.v, 0, field_bytes(c, S.prec), st));
+          CK(cudaMemsetAsync(S.p.v, 0, field_bytes(c, S.prec), st));
+          TRY(convert(c, st, P_F64, S.rh, S.prec, S.r, DWF_KC_F64));
+          TRY(norm2(c, st, S.prec, S.r, FIN_RED2));
+          TRY(pull_scalars(c, st));
+          R[k].rr_last = c->h_sc->red2;
+          if (gexec) cudaGraphExecDestroy(gexec);
+          if (graph) cudaGraphDestroy(graph);
+          gexec = nullptr;
+          graph = nullptr;
+          first_batch = true;
+          ++escalations;
+        }
+        R[k].prev_rhat2 = R[k].rhat2;
+        TRY(arm(k, tol_now, false, R[k].mode == DWF_MODE_DEFECT || failed, R[k].rr_last));
       }
-      prev_rhat2 = rhat2;
-      TRY(arm(tol_now, false, mode_now == DWF_MODE_DEFECT || failed, rr_last));
     }
     return DWF_OK;
   };
-  // phi_sp = C^dag x_hat;  phi_op = eta'_op - M5 D^{op,sp} phi_sp;  psi = S2 phi, unpacked to
-  // d_sol; then |eta - D psi| / |eta| in FP64
-  auto reconstruct = [&](double *res_full) -> dwf_status {
-    Field phi[2], psi[2], dpsi[2];
-    for (int p = 0; p < 2; ++p) {
-      TRY(get_buf(c, "phi" + std::to_string(p), P_F64, &phi[p]));
-      TRY(get_buf(c, "psi" + std::to_string(p), P_F64, &psi[p]));
-      TRY(get_buf(c, "dpsi" + std::to_string(p), P_F64, &dpsi[p]));
-    }
-    TRY(op_cdag(c, st, P_F64, S.sp, S.xh, phi[S.sp], S.w64, S.t64, DWF_KC_F64));
+
+  // ---- solution k: phi_sp = C^dag x_hat; phi_op = eta'_op - M5 D^{op,sp} phi_sp; psi = S2 phi,
+  // unpacked to sol_k; then |eta - D psi| / |eta| in FP64
+  auto reconstruct = [&](int k) -> dwf_status {
+    UseSlot use(c, sl, k);
+    TRY(prep_eta(k));
+    TRY(op_cdag(c, st, P_F64, S.sp, at(c, S.xh, k, P_F64), phi[S.sp], S.w64, S.t64, DWF_KC_F64));
     HopArgs a = hop_args(c, P_F64, S.op);
     a.in = phi[S.sp];
     a.y = etap[S.op];
@@ -1110,7 +1267,7 @@ extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_s
     for (int p = 0; p < 2; ++p) {
       TRY(smix(c, st, P_F64, S_PLAIN, phi[p], psi[p], MK_S2, 1.0, DWF_KC_F64));
       Timed t(c, st, DWF_KC_F64);
-      CK(unpack_any(P_F64, psi[p], d_sol, g, p, c->sm_count, st));
+      CK(unpack_any(P_F64, psi[p], d_sol + (size_t)k * full_doubles, g, p, c->sm_count, st));
     }
     TRY(op_full(c, st, P_F64, psi, dpsi, MK_W, MK_Z, DWF_KC_F64));
     double num = 0, den = 0;
@@ -1134,74 +1291,167 @@ extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_s
       num += c->h_sc->red;
       den += c->h_sc->red2;
     }
-    *res_full = den > 0 ? sqrt(num / den) : 0.0;
+    R[k].res_full = den > 0 ? sqrt(num / den) : 0.0;
     return DWF_OK;
   };
 
-  // the full-system residual runs a little above the Schur one (by at most cond(S1)), so the
-  // Schur system of a full solve aims at half the tolerance
-  const double tol_schur = full ? 0.5 * prm.tol : prm.tol;
-  rr_last = c->h_sc->red2;
-  TRY(arm(tol_schur, true, true, rr_last));
-  result = cg_loop(tol_schur);
-  if (result == DWF_OK && full) {
-    double res_full = 0;
-    TRY(reconstruct(&res_full));
-    // the full-system residual exceeds the Schur one by at most cond(S1); if it misses
-    // the target, tighten the Schur tolerance once and continue from x_hat
-    if (res_full > prm.tol && converged) {
-      const double tighter = tol_schur * std::min(0.1, 0.5 * prm.tol / res_full);
-      TRY(arm(tighter, false, mode_now == DWF_MODE_DEFECT, rr_last));
-      result = cg_loop(tighter);
-      if (result == DWF_OK) TRY(reconstruct(&res_full));
+  dwf_status loop_st = cg_loop(tol_schur);
+  if (loop_st != DWF_OK && loop_st != DWF_ENOCONV) return loop_st;
+  if (full) {
+    for (int k = 0; k < K; ++k) TRY(reconstruct(k));
+    // single system: if the full residual still misses the target, tighten the Schur
+    // tolerance once and continue from x_hat
+    if (K == 1 && R[0].converged && R[0].res_full > prm.tol) {
+      const double tighter = tol_schur * std::min(0.1, 0.5 * prm.tol / R[0].res_full);
+      R[0].done = R[0].converged = false;
+      TRY(arm(0, tighter, false, R[0].mode == DWF_MODE_DEFECT, R[0].rr_last));
+      loop_st = cg_loop(tighter);
+      if (loop_st != DWF_OK && loop_st != DWF_ENOCONV) return loop_st;
+      TRY(reconstruct(0));
     }
-    S_out->true_res_full = res_full;
-  } else if (result == DWF_OK || result == DWF_ENOCONV) {
-    if (full) {
-      double res_full = 0;
-      TRY(reconstruct(&res_full));
-      S_out->true_res_full = res_full;
-    } else {
-      CK(cudaMemsetAsync(d_sol, 0, (size_t)c->V4 * c->Ns * 24 * sizeof(double), st));
+  } else {
+    CK(cudaMemsetAsync(d_sol, 0, (size_t)K * full_doubles * sizeof(double), st));
+    for (int k = 0; k < K; ++k) {
       Timed t(c, st, DWF_KC_F64);
-      CK(unpack_any(P_F64, S.xh, d_sol, g, S.sp, c->sm_count, st));
+      CK(unpack_any(P_F64, at(c, S.xh, k, P_F64), d_sol + (size_t)k * full_doubles, g, S.sp, c->sm_count, st));
     }
   }
-  iters = c->h_sc->iter;
   CK(cudaEventRecord(ev1, st));
+  CK(cudaStreamSynchronize(st));
+  CK(cudaMemcpyAsync(sl.h_sc, sl.d_sc, K * sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   float ms = 0;
   cudaEventElapsedTime(&ms, ev0, ev1);
-  S_out->iters = iters;
-  S_out->restarts = restarts;
-  S_out->mode_used = mode_now;
-  S_out->converged = converged ? 1 : 0;
-  S_out->true_res = bnorm2 > 0 ? sqrt(rhat2 / bnorm2) : 0.0;
   const double n = (double)c->h * c->Ns;
-  S_out->flops = n * (iters * flops_cg_iter(c->Ns) + restarts * flops_restart(c->Ns) +
-                      (full ? flops_prep_recon(c->Ns) : 0.0));
-  S_out->time_ms = ms;
-  S_out->bytes_hop_m5 = n * (2.0 * site_bytes(S.prec) + 8.0 * link_bytes_per_site(S.prec) / 8.0 / c->Ns);
-  S_out->inner_prec_used = S.prec;
-  S_out->escalations = escalations;
-  end_profile(c, S_out);
-  S_out->kernel_launches = c->launches - launches0;
-  if (result == DWF_OK && !converged) result = fail(c, DWF_ENOCONV, "not converged");
+  end_profile(c, &S_out[0]);
+  dwf_status result = DWF_OK;
+  for (int k = 0; k < K; ++k) {
+    dwf_solve_stats &o = S_out[k];
+    if (k > 0) {
+      memcpy(o.class_ms, S_out[0].class_ms, sizeof(o.class_ms));
+      memcpy(o.class_launches, S_out[0].class_launches, sizeof(o.class_launches));
+    }
+    o.iters = sl.h_sc[k].iter;
+    o.restarts = R[k].restarts;
+    o.mode_used = R[k].mode;
+    o.converged = R[k].converged ? 1 : 0;
+    o.true_res = R[k].bnorm2 > 0 ? sqrt(R[k].rhat2 / R[k].bnorm2) : 0.0;
+    o.true_res_full = full ? R[k].res_full : 0.0;
+    o.flops = n * (o.iters * flops_cg_iter(c->Ns) + o.restarts * flops_restart(c->Ns) +
+                   (full ? flops_prep_recon(c->Ns) : 0.0));
+    o.time_ms = ms;
+    o.bytes_hop_m5 = n * (2.0 * site_bytes(S.prec) + 8.0 * link_bytes_per_site(S.prec) / 8.0 / c->Ns);
+    o.inner_prec_used = S.prec;
+    o.escalations = escalations;
+    o.kernel_launches = c->launches - launches0;
+    if (R[k].status != DWF_OK && result == DWF_OK) result = R[k].status;
+    if (!R[k].converged && result == DWF_OK) result = fail(c, DWF_ENOCONV, "not converged");
+  }
   return result;
 }
 
-extern "C" dwf_status dwf_solve(dwf_ctx *c, const double *rhs, double *sol, const dwf_solve_params *pp,
-                                dwf_solve_stats *stats) {
+dwf_status check_solve_args(dwf_ctx *c, dwf_solve_params *prm, const dwf_solve_params *pp, const void *d_rhs,
+                            const void *d_sol) {
+  if (pp) *prm = *pp;
+  else dwf_solve_params_default(prm);
+  if (!d_rhs || !d_sol || !aligned16(d_rhs) || !aligned16(d_sol))
+    return fail(c, DWF_EINVAL, "null or non-16-byte-aligned field pointer");
+  if (!valid_prec(prm->inner_prec)) return fail(c, DWF_EINVAL, "unknown inner precision");
+  if (prm->system != DWF_SYS_FULL && prm->system != DWF_SYS_NORMAL) return fail(c, DWF_EINVAL, "unknown system");
+  if (prm->schur_parity != 0 && prm->schur_parity != 1) return fail(c, DWF_EINVAL, "schur_parity must be 0 or 1");
+  if (prm->mode < DWF_MODE_AUTO || prm->mode > DWF_MODE_DEFECT) return fail(c, DWF_EINVAL, "unknown mode");
+  if (!(prm->tol > 0.0) || prm->max_iter < 1) return fail(c, DWF_EINVAL, "tol must be > 0 and max_iter >= 1");
+  if (prm->check_every < 1) prm->check_every = 8;
+  return DWF_OK;
+}
+
+}  // namespace
+
+extern "C" dwf_status dwf_solve_batch_dev(dwf_ctx *c, int nrhs, const double *d_rhs, double *d_sol,
+                                          const dwf_solve_params *pp, dwf_solve_stats *stats, void *stream) {
+  TRY(check_ctx(c));
+  if (nrhs < 1 || nrhs > 65535) return fail(c, DWF_EINVAL, "nrhs must be in 1..65535");
+  dwf_solve_params prm;
+  TRY(check_solve_args(c, &prm, pp, d_rhs, d_sol));
+  const size_t full = (size_t)c->V4 * c->Ns * 24 * sizeof(double);
+  const char *a = (const char *)d_rhs, *b = (const char *)d_sol;
+  if (a < b + nrhs * full && b < a + nrhs * full) return fail(c, DWF_EINVAL, "rhs and sol overlap");
+  std::vector<dwf_solve_stats> local;
+  if (!stats) {
+    local.resize(nrhs);
+    stats = local.data();
+  }
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  return solve_core(c, nrhs, d_rhs, d_sol, prm, stats, st);
+}
+
+extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_sol, const dwf_solve_params *pp,
+                                    dwf_solve_stats *stats, void *stream) {
+  return dwf_solve_batch_dev(c, 1, d_rhs, d_sol, pp, stats, stream);
+}
+
+extern "C" dwf_status dwf_solve_batch(dwf_ctx *c, int nrhs, const double *rhs, double *sol,
+                                      const dwf_solve_params *pp, dwf_solve_stats *stats) {
   TRY(check_ctx(c));
   if (!rhs || !sol) return fail(c, DWF_EINVAL, "null field pointer");
-  const size_t full = (size_t)c->V4 * c->Ns * 24 * sizeof(double);
+  if (nrhs < 1 || nrhs > 65535) return fail(c, DWF_EINVAL, "nrhs must be in 1..65535");
+  const size_t full = (size_t)c->V4 * c->Ns * 24 * sizeof(double) * nrhs;
   void *din, *dout;
   TRY(get_raw(c, "host_in", full, &din));
   TRY(get_raw(c, "host_out", full, &dout));
   CK(cudaMemcpyAsync(din, rhs, full, cudaMemcpyHostToDevice, c->stream));
-  dwf_status s = dwf_solve_dev(c, (const double *)din, (double *)dout, pp, stats, c->stream);
+  dwf_status s = dwf_solve_batch_dev(c, nrhs, (const double *)din, (double *)dout, pp, stats, c->stream);
   if (s != DWF_OK && s != DWF_ENOCONV) return s;
   CK(cudaMemcpyAsync(sol, dout, full, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return s;
+}
+
+extern "C" dwf_status dwf_solve(dwf_ctx *c, const double *rhs, double *sol, const dwf_solve_params *pp,
+                                dwf_solve_stats *stats) {
+  return dwf_solve_batch(c, 1, rhs, sol, pp, stats);
+}
+
+// ====================================================================== propagators
+
+extern "C" dwf_status dwf_propagator_dev(dwf_ctx *c, const int x0[4], const dwf_solve_params *pp, double *d_prop,
+                                         dwf_solve_stats *stats, void *stream) {
+  TRY(check_ctx(c));
+  if (!x0 || !d_prop || !aligned16(d_prop)) return fail(c, DWF_EINVAL, "null x0 or non-16-byte-aligned output");
+  for (int mu = 0; mu < 4; ++mu)
+    if (x0[mu] < 0 || x0[mu] >= c->dims[mu]) return fail(c, DWF_EINVAL, "source point outside the lattice");
+  dwf_solve_params prm;
+  if (pp) prm = *pp;
+  else dwf_solve_params_default(&prm);
+  prm.system = DWF_SYS_FULL;
+  cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  const size_t full = (size_t)c->V4 * c->Ns * 24 * sizeof(double);
+  void *drhs, *dsol;
+  TRY(get_raw(c, "prop_rhs", 12 * full, &drhs));
+  TRY(get_raw(c, "prop_sol", 12 * full, &dsol));
+  CK(cudaMemsetAsync(drhs, 0, 12 * full, st));
+  const long x0site = x0[0] + (long)c->dims[0] * (x0[1] + (long)c->dims[1] * (x0[2] + (long)c->dims[2] * x0[3]));
+  CK(point_sources_launch(static_cast<double *>(drhs), x0site, c->V4, c->Ns, st));
+  c->launches++;
+  dwf_status s = dwf_solve_batch_dev(c, 12, static_cast<const double *>(drhs), static_cast<double *>(dsol), &prm,
+                                     stats, st);
+  if (s != DWF_OK && s != DWF_ENOCONV) return s;
+  CK(prop_extract_launch(static_cast<const double *>(dsol), d_prop, c->V4, c->Ns, c->sm_count, st));
+  c->launches++;
+  CK(cudaStreamSynchronize(st));
+  return s;
+}
+
+extern "C" dwf_status dwf_propagator(dwf_ctx *c, const int x0[4], const dwf_solve_params *pp, double *prop,
+                                     dwf_solve_stats *stats) {
+  TRY(check_ctx(c));
+  if (!prop) return fail(c, DWF_EINVAL, "null output");
+  const size_t bytes = (size_t)c->V4 * 144 * 2 * sizeof(double);
+  void *dprop;
+  TRY(get_raw(c, "prop_out", bytes, &dprop));
+  dwf_status s = dwf_propagator_dev(c, x0, pp, static_cast<double *>(dprop), stats, c->stream);
+  if (s != DWF_OK && s != DWF_ENOCONV) return s;
+  CK(cudaMemcpyAsync(prop, dprop, bytes, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return s;
 }

@@ -47,6 +47,8 @@ struct dwf_ctx {
   std::map<std::string, dwf::Buf> bufs;
   dwf::CGScalars *d_sc = nullptr;
   dwf::CGScalars *h_sc = nullptr;  // pinned mirror
+  dwf::CGScalars *h_scb = nullptr; // pinned mirror of the scalars of a batch
+  int h_scb_cap = 0;
   double *d_part = nullptr;
   unsigned *d_ticket = nullptr;
   size_t part_len = 0;

@@ -190,7 +190,19 @@ struct HopArgs {
   CGScalars *sc;
   double *partials;
   unsigned *ticket;
+  // batches of right-hand sides: blockIdx.y selects one; its fields start fstride bytes
+  // (norms nstride floats) after the previous one's, and it has its own scalars, partial
+  // sums (part_stride doubles apart) and ticket
+  int nrhs;
+  size_t fstride, nstride;
+  size_t part_stride;
 };
+
+__device__ __forceinline__ Field field_rhs(Field f, int rb, size_t fstride, size_t nstride) {
+  if (f.v) f.v = static_cast<char *>(f.v) + rb * fstride;
+  if (f.nrm) f.nrm += rb * nstride;
+  return f;
+}
 
 // L2 prefetch of a contiguous range (an epilogue operand of this CTA's sites)
 __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
@@ -233,6 +245,11 @@ __host__ __device__ inline size_t hop_smem_bytes(int spb, int Ns, bool has_m) {
 // spinors (Eq. 12), the hop sum in packed FP32 pairs (or FP64), then the epilogue.
 template <int P, int EPI, int NSC>
 __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
+  // one right-hand side of a batch per grid row; fields are offset where they are used, so
+  // the pointers stay in parameter space instead of registers
+  const int rb = blockIdx.y;
+  auto F = [&](const Field &f) { return rb ? field_rhs(f, rb, a.fstride, a.nstride) : f; };
+  CGScalars *const sc_ = a.sc + rb;
   using T = PT<P>;
   using R = typename T::real;
   using E = EpiT<EPI>;
@@ -248,7 +265,7 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
   const bool active = sl < nsite;
   const long cb = cb0 + sl;
 
-  if (a.use_flag && a.sc->restart_flag) return;  // uniform over the grid
+  if (a.use_flag && sc_->restart_flag) return;  // uniform over the grid
 
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
   typename T::lreal *sL = reinterpret_cast<typename T::lreal *>(sm + SM::off_raw());
@@ -282,19 +299,19 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
     const uint32_t ob = (uint32_t)((size_t)nsite * T::NCH * Ns * 16);
     const size_t off = (size_t)cb0 * T::NCH * Ns * 16;
     if constexpr (EPI == E_XPAY_G5 || EPI == E_XPAY || EPI == E_M_XPAY || EPI == E_CG_UPDATE || EPI == E_RESID)
-      prefetch_l2(static_cast<const unsigned char *>(a.y.v) + off, ob);
+      prefetch_l2(static_cast<const unsigned char *>(F(a.y).v) + off, ob);
     if constexpr (EPI == E_CG_UPDATE) {
-      prefetch_l2(static_cast<const unsigned char *>(a.r.v) + off, ob);
-      prefetch_l2(static_cast<const unsigned char *>(a.x.v) + off, ob);
-      prefetch_l2(static_cast<const unsigned char *>(a.p.v) + off, ob);
+      prefetch_l2(static_cast<const unsigned char *>(F(a.r).v) + off, ob);
+      prefetch_l2(static_cast<const unsigned char *>(F(a.x).v) + off, ob);
+      prefetch_l2(static_cast<const unsigned char *>(F(a.p).v) + off, ob);
     }
-    if constexpr (EPI == E_RESID) prefetch_l2(static_cast<const unsigned char *>(a.b.v) + off, ob);
+    if constexpr (EPI == E_RESID) prefetch_l2(static_cast<const unsigned char *>(F(a.b).v) + off, ob);
   }
   // bounded wait, outcome agreed by the whole CTA before anyone acts on it
   {
     const bool ok = mbar_wait(bar, 0, kWaitTries);
     if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicExch(&a.sc->error, ERR_TMA_TIMEOUT);
+      if (tid == 0) atomicExch(&sc_->error, ERR_TMA_TIMEOUT);
       mbar_wait(bar, 0, kWaitTries);  // give the copy in flight a bounded time to land
       return;
     }
@@ -322,7 +339,7 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
 #pragma unroll
       for (int d = 0; d < 8; ++d) {
         float ps1[24];
-        load_sp_ro<P>(a.in, nb[d], s, Ns, ps1);
+        load_sp_ro<P>(F(a.in), nb[d], s, Ns, ps1);
         f2 ps[12];
 #pragma unroll
         for (int q = 0; q < 12; ++q) ps[q] = pk2(ps1[2 * q], ps1[2 * q + 1]);
@@ -346,7 +363,7 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
       R ps[24], W[18];
 #pragma unroll
       for (int d = 0; d < 8; ++d) {
-        load_sp_ro<P>(a.in, nb[d], s, Ns, ps);
+        load_sp_ro<P>(F(a.in), nb[d], s, Ns, ps);
         load_link<P>(myL + d * T::LREALS, W);
         const R S = d < 4 ? (R)-1 : (R)1;
         switch (d & 3) {
@@ -417,12 +434,12 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
     if constexpr (EPI == E_PLAIN) {
 #pragma unroll
       for (int c = 0; c < 24; ++c) acc[c] *= (R)a.coef;
-      store_sp<P>(a.out, cb, s, Ns, acc);
+      store_sp<P>(F(a.out), cb, s, Ns, acc);
     } else if constexpr (EPI == E_M) {
-      store_sp<P>(a.out, cb, s, Ns, acc);
+      store_sp<P>(F(a.out), cb, s, Ns, acc);
     } else if constexpr (EPI == E_XPAY_G5 || EPI == E_XPAY) {
       R y[24];
-      load_sp<P>(a.y, cb, s, Ns, y);
+      load_sp<P>(F(a.y), cb, s, Ns, y);
       const R cf = (R)a.coef;
 #pragma unroll
       for (int c = 0; c < 24; ++c) {
@@ -430,28 +447,28 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
         y[c] += g * acc[c];
         part += y[c] * y[c];
       }
-      store_sp<P>(a.out, cb, s, Ns, y);
+      store_sp<P>(F(a.out), cb, s, Ns, y);
     } else if constexpr (EPI == E_M_XPAY) {
       R y[24];
-      load_sp<P>(a.y, cb, s, Ns, y);
+      load_sp<P>(F(a.y), cb, s, Ns, y);
 #pragma unroll
       for (int c = 0; c < 24; ++c) y[c] += acc[c];
-      store_sp<P>(a.out, cb, s, Ns, y);
+      store_sp<P>(F(a.out), cb, s, Ns, y);
     } else if constexpr (EPI == E_CG_UPDATE) {
       // alpha = (r, r) / (p, A p) was formed once by the reduction that produced (p, A p)
       R alpha;
-      if constexpr (P == P_F64) alpha = a.sc->alpha;
-      else alpha = a.sc->alpha_f;
+      if constexpr (P == P_F64) alpha = sc_->alpha;
+      else alpha = sc_->alpha_f;
       if constexpr (!T::HALF) {
         // chunk by chunk: four operands of 16 bytes live at a time, not 4 x 24 reals
         constexpr int RPC = T::RPC;
 #pragma unroll
         for (int k = 0; k < T::NCH; ++k) {
           R y[RPC], r[RPC], xx[RPC], pp[RPC];
-          load_chunk<P>(a.y, cb, s, Ns, k, y);
-          load_chunk<P>(a.r, cb, s, Ns, k, r);
-          load_chunk<P>(a.x, cb, s, Ns, k, xx);
-          load_chunk<P>(a.p, cb, s, Ns, k, pp);
+          load_chunk<P>(F(a.y), cb, s, Ns, k, y);
+          load_chunk<P>(F(a.r), cb, s, Ns, k, r);
+          load_chunk<P>(F(a.x), cb, s, Ns, k, xx);
+          load_chunk<P>(F(a.p), cb, s, Ns, k, pp);
 #pragma unroll
           for (int j = 0; j < RPC; ++j) {
             const R ap = y[j] + acc[k * RPC + j];
@@ -459,15 +476,15 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
             xx[j] += alpha * pp[j];
             part += r[j] * r[j];
           }
-          store_chunk<P>(a.r, cb, s, Ns, k, r);
-          store_chunk<P>(a.x, cb, s, Ns, k, xx);
+          store_chunk<P>(F(a.r), cb, s, Ns, k, r);
+          store_chunk<P>(F(a.x), cb, s, Ns, k, xx);
         }
       } else {
         R y[24], r[24], xx[24], pp[24];
-        load_sp<P>(a.y, cb, s, Ns, y);
-        load_sp<P>(a.r, cb, s, Ns, r);
-        load_sp<P>(a.x, cb, s, Ns, xx);
-        load_sp<P>(a.p, cb, s, Ns, pp);
+        load_sp<P>(F(a.y), cb, s, Ns, y);
+        load_sp<P>(F(a.r), cb, s, Ns, r);
+        load_sp<P>(F(a.x), cb, s, Ns, xx);
+        load_sp<P>(F(a.p), cb, s, Ns, pp);
 #pragma unroll
         for (int c = 0; c < 24; ++c) {
           const R ap = y[c] + acc[c];
@@ -475,22 +492,22 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
           xx[c] += alpha * pp[c];
           part += r[c] * r[c];
         }
-        store_sp<P>(a.r, cb, s, Ns, r);
-        store_sp<P>(a.x, cb, s, Ns, xx);
+        store_sp<P>(F(a.r), cb, s, Ns, r);
+        store_sp<P>(F(a.x), cb, s, Ns, xx);
       }
     } else if constexpr (EPI == E_RESID) {
       R y[24], bb[24];
-      load_sp<P>(a.y, cb, s, Ns, y);
-      load_sp<P>(a.b, cb, s, Ns, bb);
+      load_sp<P>(F(a.y), cb, s, Ns, y);
+      load_sp<P>(F(a.b), cb, s, Ns, bb);
 #pragma unroll
       for (int c = 0; c < 24; ++c) {
         bb[c] -= y[c] + acc[c];
         part += bb[c] * bb[c];
       }
-      store_sp<P>(a.out, cb, s, Ns, bb);
+      store_sp<P>(F(a.out), cb, s, Ns, bb);
     }
   }
-  if constexpr (E::has_red) grid_sum<R>(part, a.partials, a.ticket, a.fin, a.sc);
+  if constexpr (E::has_red) grid_sum<R>(part, a.partials + rb * a.part_stride, a.ticket + rb, a.fin, sc_);
 }
 
 // ------------------------------------------------------------------ s-mixing kernel
@@ -510,6 +527,8 @@ struct SmixArgs {
   int Ns;
   int use_flag;
   CGScalars *sc;
+  int nrhs;               // batches of right-hand sides as in HopArgs
+  size_t fstride, nstride;
 };
 
 template <int P>
@@ -521,6 +540,9 @@ __host__ __device__ inline size_t smix_smem_bytes(int spb, int Ns, bool dual) {
 
 template <int P, int MODE>
 __global__ void __launch_bounds__(256) k_smix(const SmixArgs a) {
+  const int rb = blockIdx.y;  // one right-hand side of a batch per grid row
+  auto F = [&](const Field &f) { return rb ? field_rhs(f, rb, a.fstride, a.nstride) : f; };
+  CGScalars *const sc_ = a.sc + rb;
   using R = typename PT<P>::real;
   extern __shared__ __align__(128) unsigned char sm[];
   const int Ns = a.Ns;
@@ -529,7 +551,7 @@ __global__ void __launch_bounds__(256) k_smix(const SmixArgs a) {
   const int nthr = blockDim.x * blockDim.y;
   const long cb = (long)blockIdx.x * spb + sl;
   const bool active = cb < a.h;
-  if (a.use_flag && a.sc->restart_flag) return;
+  if (a.use_flag && sc_->restart_flag) return;
   constexpr bool dual = MODE == S_DUAL;
   R *sK = reinterpret_cast<R *>(sm);
   R *sB = reinterpret_cast<R *>(sm + ((((size_t)(dual ? 4 : 2) * Ns * Ns * sizeof(R)) + 15) & ~size_t(15)));
@@ -546,15 +568,15 @@ __global__ void __launch_bounds__(256) k_smix(const SmixArgs a) {
     if constexpr (MODE == S_CGP) {
       R r[24];
       R beta;
-      if constexpr (P == P_F64) beta = a.sc->beta;
-      else beta = a.sc->beta_f;
-      load_sp<P>(a.r, cb, s, Ns, r);
-      load_sp<P>(a.p, cb, s, Ns, v);
+      if constexpr (P == P_F64) beta = sc_->beta;
+      else beta = sc_->beta_f;
+      load_sp<P>(F(a.r), cb, s, Ns, r);
+      load_sp<P>(F(a.p), cb, s, Ns, v);
 #pragma unroll
       for (int c = 0; c < 24; ++c) v[c] = r[c] + beta * v[c];
-      store_sp<P>(a.p, cb, s, Ns, v);
+      store_sp<P>(F(a.p), cb, s, Ns, v);
     } else {
-      load_sp_ro<P>(a.in, cb, s, Ns, v);
+      load_sp_ro<P>(F(a.in), cb, s, Ns, v);
     }
     if constexpr (MODE == S_CGP || MODE == S_G5) {
 #pragma unroll
@@ -580,7 +602,7 @@ __global__ void __launch_bounds__(256) k_smix(const SmixArgs a) {
 #pragma unroll
       for (int c = 12; c < 24; ++c) o[c] += km * vv[c];
     }
-    store_sp<P>(which == 0 ? a.out : a.out2, cb, s, Ns, o);
+    store_sp<P>(which == 0 ? F(a.out) : F(a.out2), cb, s, Ns, o);
   }
 }
 
@@ -759,6 +781,34 @@ __global__ void k_neighbours(int *nbr, Geom g, int p) {
       const long site = e[0] + (long)g.d[0] * (e[1] + (long)g.d[1] * (e[2] + (long)g.d[2] * e[3]));
       nbr[cb * 8 + dir] = (int)(site >> 1);
     }
+  }
+}
+
+// ------------------------------------------------------------------ propagators
+//
+// 12 point sources at site x0 (full-lattice host layout, one after another): source
+// (beta, b) has a 1 in spin beta, colour b on the s-slice of its chirality's wall
+// (P+ spins 0,1 on s = 0, P- spins 2,3 on s = Ns - 1).
+__global__ void k_point_sources(double *rhs, long x0site, long V4, int Ns) {
+  const int k = threadIdx.x;
+  if (k >= 12) return;
+  const int beta = k / 3, b = k % 3;
+  const int s = beta < 2 ? 0 : Ns - 1;
+  rhs[(size_t)k * V4 * Ns * 24 + (((size_t)x0site * Ns + s) * 12 + 3 * beta + b) * 2] = 1.0;
+}
+
+// 4D quark field q(x) = P- psi(x, s = 0) + P+ psi(x, s = Ns - 1) of the 12 solutions, as
+// prop[site][alpha][a][beta][b] complex
+__global__ void k_prop_extract(const double *sol, double *prop, long V4, int Ns) {
+  const long n = V4 * 144;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const long site = i / 144;
+    const int r = (int)(i % 144), sink = r / 12, src = r % 12;
+    const int alpha = sink / 3, a = sink % 3;
+    const int s = alpha < 2 ? Ns - 1 : 0;
+    const double2 v = *reinterpret_cast<const double2 *>(
+        sol + (size_t)src * V4 * Ns * 24 + (((size_t)site * Ns + s) * 12 + 3 * alpha + a) * 2);
+    reinterpret_cast<double2 *>(prop)[i] = v;
   }
 }
 

@@ -46,7 +46,7 @@ cudaError_t hop_go(const HopArgs &a, cudaStream_t st) {
     configured.store(smem);
   }
   const long nblk = (a.h + spb - 1) / spb;
-  k_hop<P, EPI, NSC><<<(unsigned)nblk, dim3(a.Ns, spb), smem, st>>>(a);
+  k_hop<P, EPI, NSC><<<dim3((unsigned)nblk, a.nrhs > 1 ? a.nrhs : 1), dim3(a.Ns, spb), smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -92,7 +92,7 @@ cudaError_t smix_go(const SmixArgs &a, cudaStream_t st) {
     configured.store(smem);
   }
   const long nblk = (a.h + spb - 1) / spb;
-  k_smix<P, MODE><<<(unsigned)nblk, dim3(a.Ns, spb), smem, st>>>(a);
+  k_smix<P, MODE><<<dim3((unsigned)nblk, a.nrhs > 1 ? a.nrhs : 1), dim3(a.Ns, spb), smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -181,5 +181,7 @@ DWF_DECLARE_PREC(P_BF16)
 
 cudaError_t neighbours_launch(int *nbr, Geom g, int parity, int sm_count, cudaStream_t st);
 cudaError_t diff_norm2_launch(const VecArgs &v, int sm_count, cudaStream_t st);
+cudaError_t point_sources_launch(double *rhs, long x0site, long V4, int Ns, cudaStream_t st);
+cudaError_t prop_extract_launch(const double *sol, double *prop, long V4, int Ns, int sm_count, cudaStream_t st);
 
 }  // namespace dwf

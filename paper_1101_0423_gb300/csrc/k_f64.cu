@@ -12,6 +12,16 @@ cudaError_t neighbours_launch(int *nbr, Geom g, int parity, int sm_count, cudaSt
   return cudaGetLastError();
 }
 
+cudaError_t point_sources_launch(double *rhs, long x0site, long V4, int Ns, cudaStream_t st) {
+  k_point_sources<<<1, 32, 0, st>>>(rhs, x0site, V4, Ns);
+  return cudaGetLastError();
+}
+
+cudaError_t prop_extract_launch(const double *sol, double *prop, long V4, int Ns, int sm_count, cudaStream_t st) {
+  k_prop_extract<<<vec_grid(V4 * 144, sm_count), 256, 0, st>>>(sol, prop, V4, Ns);
+  return cudaGetLastError();
+}
+
 cudaError_t diff_norm2_launch(const VecArgs &v, int sm_count, cudaStream_t st) {
   k_diff_norm2<<<vec_grid(v.n, sm_count), 256, 0, st>>>(v);
   return cudaGetLastError();

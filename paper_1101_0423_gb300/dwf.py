@@ -111,6 +111,11 @@ def load(build_if_missing: bool = True):
         "dwf_apply_eo_dev_static": ([vp, i, i, i, vp, vp, vp], i),
         "dwf_solve": ([vp, dp, dp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats)], i),
         "dwf_solve_dev": ([vp, vp, vp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), vp], i),
+        "dwf_propagator": ([vp, ip, ctypes.POINTER(SolveParams), dp, ctypes.POINTER(SolveStats)], i),
+        "dwf_propagator_dev": ([vp, ip, ctypes.POINTER(SolveParams), vp, ctypes.POINTER(SolveStats), vp], i),
+        "dwf_solve_batch": ([vp, i, dp, dp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats)], i),
+        "dwf_solve_batch_dev": ([vp, i, vp, vp, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), vp],
+                                i),
         "dwf_last_error": ([vp], ctypes.c_char_p),
         "dwf_status_string": ([i], ctypes.c_char_p),
         "dwf_solve_params_default": ([ctypes.POINTER(SolveParams)], None),
@@ -238,6 +243,41 @@ def dwf_solve_dev(ctx, d_rhs, d_sol, params=None, stream=None, allow_noconv=Fals
     if not (allow_noconv and st == DWF_ENOCONV):
         _check(ctx, st)
     return stats.as_dict()
+
+
+def dwf_solve_batch(ctx, rhs, params=None, allow_noconv=False, **kw):
+    """rhs: array of shape (nrhs, 24*Ns*V4) (or flat).  Returns (solutions, list of stats dicts)."""
+    rhs = _f64(rhs)
+    nrhs = rhs.shape[0] if rhs.ndim > 1 else 1
+    sol = np.empty_like(rhs)
+    p = _params(params, **kw)
+    stats = (SolveStats * nrhs)()
+    st = load().dwf_solve_batch(ctx, nrhs, _dp(rhs), _dp(sol), ctypes.byref(p), stats)
+    if not (allow_noconv and st == DWF_ENOCONV):
+        _check(ctx, st)
+    return sol, [stats[k].as_dict() for k in range(nrhs)]
+
+
+def dwf_solve_batch_dev(ctx, nrhs, d_rhs, d_sol, params=None, stream=None, allow_noconv=False, **kw):
+    p = _params(params, **kw)
+    stats = (SolveStats * nrhs)()
+    st = load().dwf_solve_batch_dev(ctx, int(nrhs), _ptr(d_rhs), _ptr(d_sol), ctypes.byref(p), stats,
+                                    _stream(stream))
+    if not (allow_noconv and st == DWF_ENOCONV):
+        _check(ctx, st)
+    return [stats[k].as_dict() for k in range(nrhs)]
+
+
+def dwf_propagator(ctx, dims, x0, params=None, allow_noconv=False, **kw):
+    """Returns (prop, stats): prop[site, alpha, a, beta, b] complex128 of shape (V4, 4, 3, 4, 3)."""
+    v4 = int(np.prod(dims))
+    out = np.empty(v4 * 144 * 2)
+    p = _params(params, **kw)
+    stats = (SolveStats * 12)()
+    st = load().dwf_propagator(ctx, (ctypes.c_int * 4)(*[int(v) for v in x0]), ctypes.byref(p), _dp(out), stats)
+    if not (allow_noconv and st == DWF_ENOCONV):
+        _check(ctx, st)
+    return out.view(np.complex128).reshape(v4, 4, 3, 4, 3), [stats[k].as_dict() for k in range(12)]
 
 
 def dwf_last_error(ctx) -> str:
