@@ -250,6 +250,81 @@ def serve_measure(n, lattices, inner_prec, fractions):
     return out
 
 
+def batch_measure():
+    """12 spin-colour point sources on 24^3 x 48 x 16 Shamir (mq = 0.01): one batched solve
+    against the same 12 solved one after another; and a ragged set of 8 right-hand sides on
+    16^3 x 32 with Ns in {8,12,16,20,24,32,12,16} and masses 0.005..0.1 (different operators),
+    served concurrently against solved one after another.  FP32 inner, FP64 restarts, 1e-10."""
+    import numpy as np
+    import torch
+    from paper_1101_0423_gb300 import dwf, inputs
+    out = []
+    dims, ns, mq = (24, 24, 24, 48), 16, 0.01
+    om, sg = inputs.weights("shamir", ns)
+    U = inputs.gauge_field(dims, EPS, seed=3)
+    src = np.stack([inputs.point_source(dims, ns, spin, col) for spin in range(4) for col in range(3)])
+    stream = torch.cuda.current_stream()
+    with dwf.Context(dims, ns, M0, mq, om, sg, U) as ctx:
+        d_rhs = torch.from_numpy(src).cuda()
+        d_sol = torch.empty_like(d_rhs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st_b = dwf.dwf_solve_batch_dev(ctx.h, 12, d_rhs, d_sol, stream=stream)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        st_s = [dwf.dwf_solve_dev(ctx.h, d_rhs[k], d_sol[k], stream=stream) for k in range(12)]
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+    fl_b = sum(x["flops"] for x in st_b)
+    fl_s = sum(x["flops"] for x in st_s)
+    out.append({"workload": "12 point sources, 24^3x48xNs16 Shamir mq=0.01, fp32 inner",
+                "batched": {"solves_per_s": 12 / tb, "seconds": tb, "gflops": fl_b / tb / 1e9,
+                            "iters": [x["iters"] for x in st_b],
+                            "max_true_res_full": max(x["true_res_full"] for x in st_b)},
+                "sequential": {"solves_per_s": 12 / ts, "seconds": ts, "gflops": fl_s / ts / 1e9,
+                               "iters": [x["iters"] for x in st_s],
+                               "max_true_res_full": max(x["true_res_full"] for x in st_s)}})
+    # ragged set: different operators, served concurrently vs one after another
+    dims = (16, 16, 16, 32)
+    Ur = inputs.gauge_field(dims, EPS, seed=4)
+    nss = [8, 12, 16, 20, 24, 32, 12, 16]
+    masses = list(np.geomspace(0.005, 0.1, 8))
+    rhs = [inputs.gaussian_source(dims, n, seed=200 + i) for i, n in enumerate(nss)]
+    om_sg = [inputs.weights("shamir", n) for n in nss]
+    t0 = time.perf_counter()
+    seq_ok = 0
+    for n, m, b, (om, sg) in zip(nss, masses, rhs, om_sg):
+        with dwf.Context(dims, n, M0, m, om, sg, Ur) as ctx:
+            _, st = dwf.dwf_solve(ctx.h, b)
+            seq_ok += st["converged"]
+    ts = time.perf_counter() - t0
+    srv = dwf.dwf_server_create(hbm_budget_gb=150.0, max_inflight=8)
+    try:
+        g = dwf.dwf_server_add_gauge(srv, dims, Ur)
+        t0 = time.perf_counter()
+        tickets = [dwf.dwf_submit(srv, dims, n, M0, m, om, sg, g, b)
+                   for n, m, b, (om, sg) in zip(nss, masses, rhs, om_sg)]
+        ok = 0
+        while tickets:
+            left = []
+            for t in tickets:
+                r = dwf.dwf_poll(srv, t)
+                if r is None:
+                    left.append(t)
+                else:
+                    ok += r[1]["status"] == dwf.DWF_OK
+            tickets = left
+            time.sleep(0.002)
+        tc = time.perf_counter() - t0
+    finally:
+        dwf.dwf_server_destroy(srv)
+    out.append({"workload": "ragged 8 rhs, 16^3x32, Ns {8,12,16,20,24,32,12,16}, mq 0.005..0.1, fp32 inner",
+                "served_concurrently": {"solves_per_s": 8 / tc, "seconds": tc, "ok": ok},
+                "sequential": {"solves_per_s": 8 / ts, "seconds": ts, "ok": seq_ok}})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -259,11 +334,19 @@ def main():
     ap.add_argument("--inner", default="f32", choices=["f32", "f16", "bf16", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch", action="store_true",
+                    help="only the batched workloads: 12 point sources on 24^3x48x16, ragged 8-rhs set")
     ap.add_argument("--serve", action="store_true",
                     help="only the served sweep: 40 requests over all four lattices at 0.2..0.95 of capacity")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch:
+        from paper_1101_0423_gb300 import build as _b
+        _b.build()
+        for row in batch_measure():
+            print(json.dumps(row))
+        return
     if args.serve:
         from paper_1101_0423_gb300 import build as _b, dwf
         _b.build()
