@@ -149,8 +149,20 @@ __device__ __forceinline__ void grid_sum(V v, double *partials, unsigned *ticket
   __syncthreads();
   if (am_last) {
     __threadfence();
+    // all of this thread's partials are requested before any is added (one L2 round trip
+    // instead of one per partial: the rest of the GPU idles during this tail); the order of
+    // the additions is fixed by the grid, so the sum is reproducible
+    constexpr int U = 8;
     double s = 0;
-    for (unsigned i = tid; i < gridDim.x; i += nthr) s += __ldcg(partials + i);
+    unsigned i = tid;
+    for (; i + (U - 1) * nthr < gridDim.x; i += U * nthr) {
+      double q[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) q[u] = __ldcg(partials + i + u * nthr);
+#pragma unroll
+      for (int u = 0; u < U; ++u) s += q[u];
+    }
+    for (; i < gridDim.x; i += nthr) s += __ldcg(partials + i);
     double tot = block_sum<double>(s, ws);
     if (tid == 0) {
       finish(fin, tot, sc);
@@ -225,8 +237,11 @@ template <int P> struct HopSmem {
   __host__ __device__ static size_t end_pk(int spb) { return off_pk(spb) + (F2 ? (size_t)spb * 8 * 9 * 16 : 0); }
   // the M5 staging buffer reuses the link area, which is dead once the hop sum is formed
   __host__ __device__ static size_t off_stage(int) { return off_raw(); }
+  // one row of 24 reals per s, padded by 16 bytes so that the eight s-rows a quarter-warp
+  // stores fall in distinct bank groups; sites padded by another 16 bytes
+  static constexpr int ROW = 24 + 16 / (int)sizeof(typename PT<P>::real);
   __host__ __device__ static size_t stage(int spb, int Ns) {
-    return (size_t)spb * (Ns * 24 * sizeof(typename PT<P>::real) + 16);
+    return (size_t)spb * (Ns * ROW * sizeof(typename PT<P>::real) + 16);
   }
   __host__ __device__ static size_t off_k(int spb, int Ns) {
     const size_t a = end_pk(spb), b = off_stage(spb) + stage(spb, Ns);
@@ -381,11 +396,12 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
 
   if constexpr (E::has_m) {
     // M5-type epilogue (Sec. 3.3): out_s = sum_t K_{st} H_t per chirality; the Ns slices
-    // of a site are in this CTA, staged through shared memory (per-site stride padded by
+    // of a site are in this CTA, staged through shared memory (rows and sites padded by
     // 16 bytes against bank conflicts; the stage reuses the link area)
     R *sB = reinterpret_cast<R *>(sS);
-    const int sstride = Ns * 24 + 16 / (int)sizeof(R);
-    R *mine = sB + (size_t)sl * sstride + (size_t)s * 24;
+    constexpr int ROW = SM::ROW;
+    const int sstride = Ns * ROW + 16 / (int)sizeof(R);
+    R *mine = sB + (size_t)sl * sstride + (size_t)s * ROW;
     __syncthreads();  // every warp is done with the links the stage overwrites
 #pragma unroll
     for (int c = 0; c < 24; ++c) mine[c] = acc[c];
@@ -401,7 +417,7 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
         for (int t = 0; t < Ns; ++t) {
           const f2 kp = sK2[t * Ns + s];            // (K+[s][t], K+[s][t])
           const f2 km = sK2[Ns * Ns + t * Ns + s];  // (K-[s][t], K-[s][t])
-          const float4 *v4 = reinterpret_cast<const float4 *>(site + t * 24);
+          const float4 *v4 = reinterpret_cast<const float4 *>(site + t * ROW);
 #pragma unroll
           for (int k = 0; k < 6; ++k) {
             const float4 v = v4[k];
@@ -419,7 +435,7 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
         for (int t = 0; t < Ns; ++t) {
           const R kp = sKd[t * Ns + s];
           const R km = sKd[Ns * Ns + t * Ns + s];
-          const R *v = site + t * 24;
+          const R *v = site + t * ROW;
 #pragma unroll
           for (int c = 0; c < 12; ++c) acc[c] += kp * v[c];
 #pragma unroll
