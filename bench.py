@@ -128,41 +128,77 @@ def dist_env():
     return world, rank, local
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_replica(dims, ns, warmup, reps, barrier, q):
+    """One host core: the oracle's FP64 C C^dagger on its own copy of the workload's input."""
+    import oracle
+    from paper_1101_0423_gb300 import inputs
+    om, sg = inputs.weights("cosine", ns)
+    U = inputs.gauge_field(dims, EPS, seed=SEED)
+    x = inputs.gaussian_source(dims, ns, seed=SEED, parity=1)
+    mp, mm = oracle.m5(ns, M0, MQ, om, sg)
+    for _ in range(warmup):
+        oracle.ccdag_op(dims, ns, U, mp, mm, 1, x)
+    barrier.wait()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.ccdag_op(dims, ns, U, mp, mm, 1, x)
+    q.put((t0, time.perf_counter()))
+
+
+def oracle_on_all_cores(dims, ns, warmup, reps, cores=None):
+    """The oracle as it stands, one process per host core (spawned: no state shared with a
+    CUDA context), each applying C C^dagger to its own input; all start together behind a
+    barrier.  Returns (aggregate GFLOP/s, wall seconds of the timed region, cores)."""
+    import multiprocessing as mp_
+    import oracle
+    oracle.build()
+    cores = cores or host_cores()
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"  # one thread per replica, inherited by the spawned processes
+    ctx = mp_.get_context("spawn")
+    barrier, q = ctx.Barrier(cores), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_replica, args=(dims, ns, warmup, reps, barrier, q)) for _ in range(cores)]
+    for pr in procs:
+        pr.start()
+    spans = [q.get() for _ in procs]
+    for pr in procs:
+        pr.join()
+    wall = max(t for _, t in spans) - min(t for t, _ in spans)
+    n = dims[0] * dims[1] * dims[2] * dims[3] // 2 * ns
+    return cores * reps * flops_ccdag(n, ns) / wall / 1e9, wall, cores
+
+
 def run_reference(args):
-    """The oracle, as it stands, on the host cores: one FP64 C C^dag application per step."""
+    """The oracle, as it stands, on all host cores: each step is one FP64 C C^dag application
+    per core (independent replicas, the CPU analogue of the replica scaling on GPUs)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
-
-    import oracle
-    from paper_1101_0423_gb300 import inputs
-    oracle.build()
-    om, sg = inputs.weights("cosine", NS)
-    U = inputs.gauge_field(DIMS, EPS, seed=SEED)
-    x = inputs.gaussian_source(DIMS, NS, seed=SEED, parity=1)
-    mp, mm = oracle.m5(NS, M0, MQ, om, sg)
-    n = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2 * NS
-    for _ in range(args.warmup):
-        oracle.ccdag_op(DIMS, NS, U, mp, mm, 1, x)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.ccdag_op(DIMS, NS, U, mp, mm, 1, x)
-    dt = time.perf_counter() - t0
-    gf = args.steps * flops_ccdag(n, NS) / dt / 1e9
-    sample = f"{args.steps} FP64 C C^dagger applications on 16^3x32x16 (oracle, single thread)"
+    gf, wall, cores = oracle_on_all_cores(DIMS, NS, args.warmup, args.steps)
+    sample = (f"{args.steps} FP64 C C^dagger applications on 16^3x32x16 per host core, "
+              f"{cores} cores in parallel (oracle, one thread each)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": gf, "unit": "GFLOP/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "C C^dagger application"},
-        "cpu_baseline": {"value": gf, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": gf, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": gf, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
-def cpu_baseline_sample():
-    """Oracle timed on one host core on a bounded sample: one FP64 C C^dagger application."""
+def cpu_baseline_sample(gpu_iters, gpu_restarts):
+    """The oracle on the host cores, bounded samples: one FP64 C C^dagger application on one
+    core (the line's value) and on every core at once; the whole 4^4x8 normal-equation solve;
+    and the 16^3x32x16 solve time extrapolated from the C C^dagger cost and the GPU solve's
+    iteration and restart counts (one C C^dagger each; labelled as extrapolated)."""
     import oracle
     from paper_1101_0423_gb300 import inputs
     oracle.build()
@@ -174,9 +210,27 @@ def cpu_baseline_sample():
     t0 = time.perf_counter()
     oracle.ccdag_op(DIMS, NS, U, mp, mm, 1, x)
     dt = time.perf_counter() - t0
+    gf_all, wall_all, cores = oracle_on_all_cores(DIMS, NS, 0, 1)
+    # 4^4 x 8 Shamir normal equations on even sites (the small workload), solved whole
+    d0, ns0 = (4, 4, 4, 4), 8
+    om0, sg0 = inputs.weights("shamir", ns0)
+    mp0, mm0 = oracle.m5(ns0, M0, 0.05, om0, sg0)
+    U0 = inputs.gauge_field(d0, 0.3, seed=1)
+    b0 = inputs.gaussian_source(d0, ns0, seed=1, parity=0)
+    t1 = time.perf_counter()
+    _, it0, res0 = oracle.cg(d0, ns0, U0, mp0, mm0, 0, b0, tol=1e-10)
+    dt0 = time.perf_counter() - t1
+    ops = gpu_iters + gpu_restarts
     return {"value": flops_ccdag(n, NS) / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
             "sample": "one FP64 C C^dagger application on 16^3x32x16 (single thread), "
-                      f"{dt:.1f} s; same flop count as the GPU's CG iterations"}
+                      f"{dt:.1f} s; same flop count as the GPU's CG iterations",
+            "all_cores": {"value": gf_all, "unit": "GFLOP/s", "cores": cores,
+                          "sample": f"one FP64 C C^dagger per core, {cores} cores at once, {wall_all:.1f} s"},
+            "small_solve": {"seconds": dt0, "iters": it0, "true_res": res0,
+                            "sample": "4^4x8 Shamir normal equations, FP64 CG to 1e-10 (single thread)"},
+            "extrapolated_solve_s": {"one_core": ops * dt, "all_cores": ops * flops_ccdag(n, NS) / (gf_all * 1e9),
+                                     "basis": f"{gpu_iters} iterations + {gpu_restarts} restarts of the GPU solve, "
+                                              "one C C^dagger each (extrapolated, not run)"}}
 
 
 # ---------------------------------------------------------------- served workload
@@ -499,7 +553,7 @@ def main():
                                    "mq U[0.005,0.1] x {shamir,borici,cosine}, bf16 inner, tol 1e-10, "
                                    "Poisson arrivals at 0.8 x single-stream capacity, 4 slots, 150 GB budget"}
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline_sample()
+        out["cpu_baseline"] = cpu_baseline_sample(s0["iters"], s0["restarts"])
     print(json.dumps(out))
     ctx.close()
     if world > 1:
