@@ -225,39 +225,54 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(
 
 // dynamic shared memory of k_hop, in bytes:
 //   [mbarrier, 64 B][links as copied][neighbour indices][links packed for f32x2][stage][K]
-// FP32-arithmetic kernels (F32, fp16, bf16) expand each link once per CTA into nine
-// 16-byte entries (wr, wr, -wi, wi) -- the 16-bit forms rebuild their third row there --
-// and keep K duplicated as (k, k) pairs; FP64 kernels use the links as copied.
+// FP32-arithmetic kernels (F32, fp16, bf16) expand each tile's links into nine 16-byte
+// entries (wr, wr, -wi, wi) -- the 16-bit forms rebuild their third row there -- and keep K
+// duplicated as (k, k) pairs; FP64 kernels use the links as copied.
+//
+// Layout: mbarriers; `nb` buffers of raw links and of neighbour indices (filled by TMA bulk
+// copies: two when a persistent CTA receives the next tile while computing this one); the
+// tile's expanded links; K.  The M5 staging rows overlay the link buffers from the start
+// (kernels with an M5 epilogue take one tile per CTA, so all of them are dead by then).
+// Shared memory is kept small on purpose: what the CTAs leave of the SM's 256 KB is the L1
+// that holds the neighbour gathers in flight.
 template <int P> struct HopSmem {
   static constexpr bool F2 = !(P == P_F64);
-  __host__ __device__ static size_t raw(int spb) { return (size_t)spb * 8 * PT<P>::LREALS * sizeof(typename PT<P>::lreal); }
-  __host__ __device__ static size_t off_raw() { return 64; }
-  __host__ __device__ static size_t off_nbr(int spb) { return off_raw() + align16(raw(spb)); }
-  __host__ __device__ static size_t off_pk(int spb) { return off_nbr(spb) + align16((size_t)spb * 8 * 4); }
-  __host__ __device__ static size_t end_pk(int spb) { return off_pk(spb) + (F2 ? (size_t)spb * 8 * 9 * 16 : 0); }
-  // the M5 staging buffer reuses the link area, which is dead once the hop sum is formed
-  __host__ __device__ static size_t off_stage(int) { return off_raw(); }
+  using RL = typename PT<P>::real;
+  __host__ __device__ static size_t raw(int nsite) {
+    return (size_t)nsite * 8 * PT<P>::LREALS * sizeof(typename PT<P>::lreal);
+  }
+  __host__ __device__ static size_t off_raw(int spb, int b) { return 64 + (size_t)b * align16(raw(spb)); }
+  __host__ __device__ static size_t off_nbr(int spb, int nb, int b) {
+    return 64 + (size_t)nb * align16(raw(spb)) + (size_t)b * align16((size_t)spb * 8 * 4);
+  }
+  __host__ __device__ static size_t off_exp(int spb, int nb) {
+    return 64 + (size_t)nb * (align16(raw(spb)) + align16((size_t)spb * 8 * 4));
+  }
   // one row of 24 reals per s, padded by 16 bytes so that the eight s-rows a quarter-warp
   // stores fall in distinct bank groups; sites padded by another 16 bytes
-  static constexpr int ROW = 24 + 16 / (int)sizeof(typename PT<P>::real);
-  __host__ __device__ static size_t stage(int spb, int Ns) {
-    return (size_t)spb * (Ns * ROW * sizeof(typename PT<P>::real) + 16);
+  static constexpr int ROW = 24 + 16 / (int)sizeof(RL);
+  __host__ __device__ static size_t stage(int spb, int Ns) { return (size_t)spb * (Ns * ROW * sizeof(RL) + 16); }
+  __host__ __device__ static size_t off_k(int spb, int Ns, int nb, bool has_m) {
+    const size_t e = off_exp(spb, nb) + (F2 ? (size_t)spb * 8 * 9 * 16 : 0);
+    const size_t st = has_m ? 64 + stage(spb, Ns) : 0;
+    return align16(e > st ? e : st);
   }
-  __host__ __device__ static size_t off_k(int spb, int Ns) {
-    const size_t a = end_pk(spb), b = off_stage(spb) + stage(spb, Ns);
-    return align16(a > b ? a : b);
-  }
-  __host__ __device__ static size_t bytes(int spb, int Ns, bool has_m) {
-    return off_k(spb, Ns) + (has_m ? align16((size_t)2 * Ns * Ns * (F2 ? 8 : sizeof(double))) : 0);
+  __host__ __device__ static size_t bytes(int spb, int Ns, int nb, bool has_m) {
+    return off_k(spb, Ns, nb, has_m) + (has_m ? align16((size_t)2 * Ns * Ns * (F2 ? 8 : sizeof(double))) : 0);
   }
 };
-template <int P>
-__host__ __device__ inline size_t hop_smem_bytes(int spb, int Ns, bool has_m) {
-  return HopSmem<P>::bytes(spb, Ns, has_m);
+// kernels without an M5 epilogue run persistent CTAs (measured: hop_xpay 96 -> 79 us); the
+// M5 kernels keep one tile per CTA and the smaller footprint (a double-buffered persistent
+// form took hop_m5 93 -> 104 us and hop_update 158 -> 188 us by shrinking the L1)
+template <int EPI> constexpr bool hop_persistent() { return !EpiT<EPI>::has_m; }
+template <int P, int EPI>
+__host__ __device__ inline size_t hop_smem_bytes(int spb, int Ns) {
+  return HopSmem<P>::bytes(spb, Ns, hop_persistent<EPI>() ? 2 : 1, EpiT<EPI>::has_m);
 }
 
-// k_hop: one thread per (site, s), CTA = (Ns, spb).  Eight gathers of the neighbours'
-// spinors (Eq. 12), the hop sum in packed FP32 pairs (or FP64), then the epilogue.
+// k_hop: one thread per (site, s), CTA = (Ns, spb) = one tile of spb sites; a grid of as
+// many CTAs as fit on the GPU at once walks all tiles.  Per tile: eight gathers of the
+// neighbours' spinors (Eq. 12), the hop sum in packed FP32 pairs (or FP64), the epilogue.
 template <int P, int EPI, int NSC>
 __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
   // one right-hand side of a batch per grid row; fields are offset where they are used, so
@@ -275,23 +290,49 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
   const int s = threadIdx.x, sl = threadIdx.y, spb = blockDim.y;
   const int tid = lin_tid();
   const int nthr = nthreads();
-  const long cb0 = (long)blockIdx.x * spb;
-  const int nsite = (int)min((long)spb, a.h - cb0);
-  const bool active = sl < nsite;
-  const long cb = cb0 + sl;
+  const long ntile = (a.h + spb - 1) / spb;
 
   if (a.use_flag && sc_->restart_flag) return;  // uniform over the grid
 
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
-  typename T::lreal *sL = reinterpret_cast<typename T::lreal *>(sm + SM::off_raw());
-  int *sN = reinterpret_cast<int *>(sm + SM::off_nbr(spb));
-  float4 *sP = reinterpret_cast<float4 *>(sm + SM::off_pk(spb));
-  unsigned char *sS = sm + SM::off_stage(spb);
-  unsigned char *sKb = sm + SM::off_k(spb, Ns);
+  constexpr bool PST = hop_persistent<EPI>();
+  constexpr int NB = PST ? 2 : 1;  // link / neighbour buffers
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sm);  // bar[b]: buffer b's copies landed
+  float4 *sP = reinterpret_cast<float4 *>(sm + SM::off_exp(spb, NB));
+  unsigned char *sS = sm + 64;
+  unsigned char *sKb = sm + SM::off_k(spb, Ns, NB, E::has_m);
+  auto sLb = [&](int b) { return reinterpret_cast<typename T::lreal *>(sm + SM::off_raw(spb, b)); };
+  auto sNb = [&](int b) { return reinterpret_cast<int *>(sm + SM::off_nbr(spb, NB, b)); };
 
-  // the CTA's links arrive with one TMA bulk copy (nsite * 8 links, contiguous, 16-byte sized)
-  if (tid == 0) mbar_init(bar, 1);
-  for (int i = tid; i < nsite * 8; i += nthr) sN[i] = __ldg(a.nbr + cb0 * 8 + i);
+  // tile t's links and neighbour indices arrive in buffer b with two TMA bulk copies (both
+  // contiguous and 16-byte sized); its epilogue operands are prefetched into L2 when the
+  // tile starts
+  auto issue = [&](long t, int b) {
+    const long c0 = t * spb;
+    const int ns_t = (int)min((long)spb, a.h - c0);
+    const uint32_t lbytes = (uint32_t)SM::raw(ns_t), nbytes = (uint32_t)ns_t * 8 * 4;
+    mbar_expect_tx(bar + b, lbytes + nbytes);
+    bulk_g2s(sLb(b), static_cast<const typename T::lreal *>(a.gauge) + (size_t)c0 * 8 * T::LREALS, lbytes, bar + b);
+    bulk_g2s(sNb(b), a.nbr + c0 * 8, nbytes, bar + b);
+  };
+  auto prefetch_ops = [&](long t) {
+    const long c0 = t * spb;
+    const int ns_t = (int)min((long)spb, a.h - c0);
+    const uint32_t ob = (uint32_t)((size_t)ns_t * T::NCH * Ns * 16);
+    const size_t off = (size_t)c0 * T::NCH * Ns * 16;
+    if constexpr (EPI == E_XPAY_G5 || EPI == E_XPAY || EPI == E_M_XPAY || EPI == E_CG_UPDATE || EPI == E_RESID)
+      prefetch_l2(static_cast<const unsigned char *>(F(a.y).v) + off, ob);
+    if constexpr (EPI == E_CG_UPDATE) {
+      prefetch_l2(static_cast<const unsigned char *>(F(a.r).v) + off, ob);
+      prefetch_l2(static_cast<const unsigned char *>(F(a.x).v) + off, ob);
+      prefetch_l2(static_cast<const unsigned char *>(F(a.p).v) + off, ob);
+    }
+    if constexpr (EPI == E_RESID) prefetch_l2(static_cast<const unsigned char *>(F(a.b).v) + off, ob);
+  };
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    if constexpr (PST) mbar_init(bar + 1, 1);
+  }
   if constexpr (E::has_m) {
     if constexpr (F2) {
       const float *Kg = static_cast<const float *>(a.K);
@@ -308,219 +349,238 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
   }
   __syncthreads();
   if (tid == 0) {
-    const uint32_t lbytes = (uint32_t)SM::raw(nsite);
-    mbar_expect_tx(bar, lbytes);
-    bulk_g2s(sL, static_cast<const typename T::lreal *>(a.gauge) + (size_t)cb0 * 8 * T::LREALS, lbytes, bar);
-    const uint32_t ob = (uint32_t)((size_t)nsite * T::NCH * Ns * 16);
-    const size_t off = (size_t)cb0 * T::NCH * Ns * 16;
-    if constexpr (EPI == E_XPAY_G5 || EPI == E_XPAY || EPI == E_M_XPAY || EPI == E_CG_UPDATE || EPI == E_RESID)
-      prefetch_l2(static_cast<const unsigned char *>(F(a.y).v) + off, ob);
-    if constexpr (EPI == E_CG_UPDATE) {
-      prefetch_l2(static_cast<const unsigned char *>(F(a.r).v) + off, ob);
-      prefetch_l2(static_cast<const unsigned char *>(F(a.x).v) + off, ob);
-      prefetch_l2(static_cast<const unsigned char *>(F(a.p).v) + off, ob);
-    }
-    if constexpr (EPI == E_RESID) prefetch_l2(static_cast<const unsigned char *>(F(a.b).v) + off, ob);
-  }
-  // bounded wait, outcome agreed by the whole CTA before anyone acts on it
-  {
-    const bool ok = mbar_wait(bar, 0, kWaitTries);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicExch(&sc_->error, ERR_TMA_TIMEOUT);
-      mbar_wait(bar, 0, kWaitTries);  // give the copy in flight a bounded time to land
-      return;
-    }
-  }
-  if constexpr (F2) {
-    // expand every link once: nine (wr, wr, -wi, wi) entries; rebuild row 3 of 16-bit links
-    for (int l = tid; l < nsite * 8; l += nthr) {
-      float W[18];
-      load_link<P>(sL + (size_t)l * T::LREALS, W);
-#pragma unroll
-      for (int e = 0; e < 9; ++e) sP[(size_t)l * 9 + e] = make_float4(W[2 * e], W[2 * e], -W[2 * e + 1], W[2 * e + 1]);
-    }
-    __syncthreads();
+    issue(blockIdx.x, 0);
+    prefetch_ops(blockIdx.x);
   }
 
-  R acc[24];
-  if (active) {
-    const int *nb = sN + sl * 8;
-    if constexpr (F2) {
-      f2 ac2[12];
-#pragma unroll
-      for (int q = 0; q < 12; ++q) ac2[q] = pk2(0.f, 0.f);
-      const SignPairs fw = sign_pairs(-1.f), bw = sign_pairs(1.f);
-      const float4 *myP = sP + (size_t)sl * 8 * 9;
-#pragma unroll
-      for (int d = 0; d < 8; ++d) {
-        float ps1[24];
-        load_sp_ro<P>(F(a.in), nb[d], s, Ns, ps1);
-        f2 ps[12];
-#pragma unroll
-        for (int q = 0; q < 12; ++q) ps[q] = pk2(ps1[2 * q], ps1[2 * q + 1]);
-        switch (d) {  // forward hops (1 - g_mu), then backward hops (1 + g_mu)
-          case 0: hop_dir_f2s<0>(ac2, ps, myP, fw); break;
-          case 1: hop_dir_f2s<1>(ac2, ps, myP + 9, fw); break;
-          case 2: hop_dir_f2s<2>(ac2, ps, myP + 18, fw); break;
-          case 3: hop_dir_f2s<3>(ac2, ps, myP + 27, fw); break;
-          case 4: hop_dir_f2s<0>(ac2, ps, myP + 36, bw); break;
-          case 5: hop_dir_f2s<1>(ac2, ps, myP + 45, bw); break;
-          case 6: hop_dir_f2s<2>(ac2, ps, myP + 54, bw); break;
-          default: hop_dir_f2s<3>(ac2, ps, myP + 63, bw); break;
+  // tiles blockIdx.x, blockIdx.x + gridDim.x, ... in this order, so that the CTA's share of
+  // a reduction is summed in a fixed order (one tile per CTA unless persistent)
+  R part = 0;
+  int it = 0;
+  for (long tile = blockIdx.x; tile < ntile; tile += gridDim.x, ++it) {
+    const int bsel = PST ? (it & 1) : 0;
+    const uint32_t par = PST ? (uint32_t)((it >> 1) & 1) : (uint32_t)(it & 1);
+    const long cb0 = tile * spb;
+    const int nsite = (int)min((long)spb, a.h - cb0);
+    const bool active = sl < nsite;
+    const long cb = cb0 + sl;
+    const typename T::lreal *sL = sLb(bsel);
+    const int *sN = sNb(bsel);
+    if constexpr (!PST) {
+      if (it > 0) {  // one buffer: the previous tile must be finished before it is refilled
+        __syncthreads();
+        if (tid == 0) {
+          issue(tile, 0);
+          prefetch_ops(tile);
         }
       }
+    }
+    // bounded wait, outcome agreed by the whole CTA before anyone acts on it; the barrier
+    // also ends every thread's use of the previous tile's buffers and staging rows
+    {
+      const bool ok = mbar_wait(bar + bsel, par, kWaitTries);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(&sc_->error, ERR_TMA_TIMEOUT);
+        mbar_wait(bar + bsel, par, kWaitTries);  // the copy in flight
+        return;
+      }
+    }
+    if constexpr (PST) {
+      // the other buffer held the previous tile, consumed before the barrier above
+      if (tid == 0) {
+        if (tile + gridDim.x < ntile) issue(tile + gridDim.x, bsel ^ 1);
+        if (it > 0) prefetch_ops(tile);
+      }
+    }
+    if constexpr (F2) {
+      // expand every link once: nine (wr, wr, -wi, wi) entries; rebuild row 3 of 16-bit links
+      for (int l = tid; l < nsite * 8; l += nthr) {
+        float W[18];
+        load_link<P>(sL + (size_t)l * T::LREALS, W);
 #pragma unroll
-      for (int q = 0; q < 12; ++q) upk2(ac2[q], acc[2 * q], acc[2 * q + 1]);
+        for (int e = 0; e < 9; ++e) sP[(size_t)l * 9 + e] = make_float4(W[2 * e], W[2 * e], -W[2 * e + 1], W[2 * e + 1]);
+      }
+      __syncthreads();
+    }
+
+    R acc[24];
+    if (active) {
+      const int *nb = sN + sl * 8;
+      if constexpr (F2) {
+        f2 ac2[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) ac2[q] = pk2(0.f, 0.f);
+        const SignPairs fw = sign_pairs(-1.f), bw = sign_pairs(1.f);
+        const float4 *myP = sP + (size_t)sl * 8 * 9;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+          float ps1[24];
+          load_sp_ro<P>(F(a.in), nb[d], s, Ns, ps1);
+          f2 ps[12];
+#pragma unroll
+          for (int q = 0; q < 12; ++q) ps[q] = pk2(ps1[2 * q], ps1[2 * q + 1]);
+          switch (d) {  // forward hops (1 - g_mu), then backward hops (1 + g_mu)
+            case 0: hop_dir_f2s<0>(ac2, ps, myP, fw); break;
+            case 1: hop_dir_f2s<1>(ac2, ps, myP + 9, fw); break;
+            case 2: hop_dir_f2s<2>(ac2, ps, myP + 18, fw); break;
+            case 3: hop_dir_f2s<3>(ac2, ps, myP + 27, fw); break;
+            case 4: hop_dir_f2s<0>(ac2, ps, myP + 36, bw); break;
+            case 5: hop_dir_f2s<1>(ac2, ps, myP + 45, bw); break;
+            case 6: hop_dir_f2s<2>(ac2, ps, myP + 54, bw); break;
+            default: hop_dir_f2s<3>(ac2, ps, myP + 63, bw); break;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 12; ++q) upk2(ac2[q], acc[2 * q], acc[2 * q + 1]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 24; ++c) acc[c] = 0;
+        const typename T::lreal *myL = sL + (size_t)sl * 8 * T::LREALS;
+        R ps[24], W[18];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+          load_sp_ro<P>(F(a.in), nb[d], s, Ns, ps);
+          load_link<P>(myL + d * T::LREALS, W);
+          const R S = d < 4 ? (R)-1 : (R)1;
+          switch (d & 3) {
+            case 0: hop_dir_s<0>(acc, ps, W, S); break;
+            case 1: hop_dir_s<1>(acc, ps, W, S); break;
+            case 2: hop_dir_s<2>(acc, ps, W, S); break;
+            default: hop_dir_s<3>(acc, ps, W, S); break;
+          }
+        }
+      }
     } else {
 #pragma unroll
       for (int c = 0; c < 24; ++c) acc[c] = 0;
-      const typename T::lreal *myL = sL + (size_t)sl * 8 * T::LREALS;
-      R ps[24], W[18];
-#pragma unroll
-      for (int d = 0; d < 8; ++d) {
-        load_sp_ro<P>(F(a.in), nb[d], s, Ns, ps);
-        load_link<P>(myL + d * T::LREALS, W);
-        const R S = d < 4 ? (R)-1 : (R)1;
-        switch (d & 3) {
-          case 0: hop_dir_s<0>(acc, ps, W, S); break;
-          case 1: hop_dir_s<1>(acc, ps, W, S); break;
-          case 2: hop_dir_s<2>(acc, ps, W, S); break;
-          default: hop_dir_s<3>(acc, ps, W, S); break;
-        }
-      }
     }
-  } else {
-#pragma unroll
-    for (int c = 0; c < 24; ++c) acc[c] = 0;
-  }
 
-  if constexpr (E::has_m) {
-    // M5-type epilogue (Sec. 3.3): out_s = sum_t K_{st} H_t per chirality; the Ns slices
-    // of a site are in this CTA, staged through shared memory (rows and sites padded by
-    // 16 bytes against bank conflicts; the stage reuses the link area)
-    R *sB = reinterpret_cast<R *>(sS);
-    constexpr int ROW = SM::ROW;
-    const int sstride = Ns * ROW + 16 / (int)sizeof(R);
-    R *mine = sB + (size_t)sl * sstride + (size_t)s * ROW;
-    __syncthreads();  // every warp is done with the links the stage overwrites
+    if constexpr (E::has_m) {
+      // M5-type epilogue (Sec. 3.3): out_s = sum_t K_{st} H_t per chirality; the Ns slices
+      // of a site are in this CTA, staged through shared memory (rows and sites padded by
+      // 16 bytes against bank conflicts; the stage overlays the link buffers)
+      R *sB = reinterpret_cast<R *>(sS);
+      constexpr int ROW = SM::ROW;
+      const int sstride = Ns * ROW + 16 / (int)sizeof(R);
+      R *mine = sB + (size_t)sl * sstride + (size_t)s * ROW;
+      __syncthreads();  // every warp is done with the links the stage overwrites
 #pragma unroll
-    for (int c = 0; c < 24; ++c) mine[c] = acc[c];
-    __syncthreads();
-    if (active) {
-      const R *site = sB + (size_t)sl * sstride;
-      if constexpr (F2) {
-        const f2 *sK2 = reinterpret_cast<const f2 *>(sKb);
-        f2 o[12];
+      for (int c = 0; c < 24; ++c) mine[c] = acc[c];
+      __syncthreads();
+      if (active) {
+        const R *site = sB + (size_t)sl * sstride;
+        if constexpr (F2) {
+          const f2 *sK2 = reinterpret_cast<const f2 *>(sKb);
+          f2 o[12];
 #pragma unroll
-        for (int q = 0; q < 12; ++q) o[q] = pk2(0.f, 0.f);
+          for (int q = 0; q < 12; ++q) o[q] = pk2(0.f, 0.f);
 #pragma unroll 4
-        for (int t = 0; t < Ns; ++t) {
-          const f2 kp = sK2[t * Ns + s];            // (K+[s][t], K+[s][t])
-          const f2 km = sK2[Ns * Ns + t * Ns + s];  // (K-[s][t], K-[s][t])
-          const float4 *v4 = reinterpret_cast<const float4 *>(site + t * ROW);
+          for (int t = 0; t < Ns; ++t) {
+            const f2 kp = sK2[t * Ns + s];            // (K+[s][t], K+[s][t])
+            const f2 km = sK2[Ns * Ns + t * Ns + s];  // (K-[s][t], K-[s][t])
+            const float4 *v4 = reinterpret_cast<const float4 *>(site + t * ROW);
 #pragma unroll
-          for (int k = 0; k < 6; ++k) {
-            const float4 v = v4[k];
-            const f2 kk = k < 3 ? kp : km;
-            o[2 * k] = fma2(kk, pk2(v.x, v.y), o[2 * k]);
-            o[2 * k + 1] = fma2(kk, pk2(v.z, v.w), o[2 * k + 1]);
+            for (int k = 0; k < 6; ++k) {
+              const float4 v = v4[k];
+              const f2 kk = k < 3 ? kp : km;
+              o[2 * k] = fma2(kk, pk2(v.x, v.y), o[2 * k]);
+              o[2 * k + 1] = fma2(kk, pk2(v.z, v.w), o[2 * k + 1]);
+            }
           }
-        }
 #pragma unroll
-        for (int q = 0; q < 12; ++q) upk2(o[q], acc[2 * q], acc[2 * q + 1]);
-      } else {
-        const double *sKd = reinterpret_cast<const double *>(sKb);
+          for (int q = 0; q < 12; ++q) upk2(o[q], acc[2 * q], acc[2 * q + 1]);
+        } else {
+          const double *sKd = reinterpret_cast<const double *>(sKb);
 #pragma unroll
-        for (int c = 0; c < 24; ++c) acc[c] = 0;
-        for (int t = 0; t < Ns; ++t) {
-          const R kp = sKd[t * Ns + s];
-          const R km = sKd[Ns * Ns + t * Ns + s];
-          const R *v = site + t * ROW;
+          for (int c = 0; c < 24; ++c) acc[c] = 0;
+          for (int t = 0; t < Ns; ++t) {
+            const R kp = sKd[t * Ns + s];
+            const R km = sKd[Ns * Ns + t * Ns + s];
+            const R *v = site + t * ROW;
 #pragma unroll
-          for (int c = 0; c < 12; ++c) acc[c] += kp * v[c];
+            for (int c = 0; c < 12; ++c) acc[c] += kp * v[c];
 #pragma unroll
-          for (int c = 12; c < 24; ++c) acc[c] += km * v[c];
+            for (int c = 12; c < 24; ++c) acc[c] += km * v[c];
+          }
         }
       }
     }
-  }
-
-  R part = 0;
-  if (active) {
-    if constexpr (EPI == E_PLAIN) {
+    if (active) {
+      if constexpr (EPI == E_PLAIN) {
 #pragma unroll
-      for (int c = 0; c < 24; ++c) acc[c] *= (R)a.coef;
-      store_sp<P>(F(a.out), cb, s, Ns, acc);
-    } else if constexpr (EPI == E_M) {
-      store_sp<P>(F(a.out), cb, s, Ns, acc);
-    } else if constexpr (EPI == E_XPAY_G5 || EPI == E_XPAY) {
-      R y[24];
-      load_sp<P>(F(a.y), cb, s, Ns, y);
-      const R cf = (R)a.coef;
-#pragma unroll
-      for (int c = 0; c < 24; ++c) {
-        const R g = (EPI == E_XPAY_G5 && c >= 12) ? -cf : cf;
-        y[c] += g * acc[c];
-        part += y[c] * y[c];
-      }
-      store_sp<P>(F(a.out), cb, s, Ns, y);
-    } else if constexpr (EPI == E_M_XPAY) {
-      R y[24];
-      load_sp<P>(F(a.y), cb, s, Ns, y);
-#pragma unroll
-      for (int c = 0; c < 24; ++c) y[c] += acc[c];
-      store_sp<P>(F(a.out), cb, s, Ns, y);
-    } else if constexpr (EPI == E_CG_UPDATE) {
-      // alpha = (r, r) / (p, A p) was formed once by the reduction that produced (p, A p)
-      R alpha;
-      if constexpr (P == P_F64) alpha = sc_->alpha;
-      else alpha = sc_->alpha_f;
-      if constexpr (!T::HALF) {
-        // chunk by chunk: four operands of 16 bytes live at a time, not 4 x 24 reals
-        constexpr int RPC = T::RPC;
-#pragma unroll
-        for (int k = 0; k < T::NCH; ++k) {
-          R y[RPC], r[RPC], xx[RPC], pp[RPC];
-          load_chunk<P>(F(a.y), cb, s, Ns, k, y);
-          load_chunk<P>(F(a.r), cb, s, Ns, k, r);
-          load_chunk<P>(F(a.x), cb, s, Ns, k, xx);
-          load_chunk<P>(F(a.p), cb, s, Ns, k, pp);
-#pragma unroll
-          for (int j = 0; j < RPC; ++j) {
-            const R ap = y[j] + acc[k * RPC + j];
-            r[j] -= alpha * ap;
-            xx[j] += alpha * pp[j];
-            part += r[j] * r[j];
-          }
-          store_chunk<P>(F(a.r), cb, s, Ns, k, r);
-          store_chunk<P>(F(a.x), cb, s, Ns, k, xx);
-        }
-      } else {
-        R y[24], r[24], xx[24], pp[24];
+        for (int c = 0; c < 24; ++c) acc[c] *= (R)a.coef;
+        store_sp<P>(F(a.out), cb, s, Ns, acc);
+      } else if constexpr (EPI == E_M) {
+        store_sp<P>(F(a.out), cb, s, Ns, acc);
+      } else if constexpr (EPI == E_XPAY_G5 || EPI == E_XPAY) {
+        R y[24];
         load_sp<P>(F(a.y), cb, s, Ns, y);
-        load_sp<P>(F(a.r), cb, s, Ns, r);
-        load_sp<P>(F(a.x), cb, s, Ns, xx);
-        load_sp<P>(F(a.p), cb, s, Ns, pp);
+        const R cf = (R)a.coef;
 #pragma unroll
         for (int c = 0; c < 24; ++c) {
-          const R ap = y[c] + acc[c];
-          r[c] -= alpha * ap;
-          xx[c] += alpha * pp[c];
-          part += r[c] * r[c];
+          const R g = (EPI == E_XPAY_G5 && c >= 12) ? -cf : cf;
+          y[c] += g * acc[c];
+          part += y[c] * y[c];
         }
-        store_sp<P>(F(a.r), cb, s, Ns, r);
-        store_sp<P>(F(a.x), cb, s, Ns, xx);
-      }
-    } else if constexpr (EPI == E_RESID) {
-      R y[24], bb[24];
-      load_sp<P>(F(a.y), cb, s, Ns, y);
-      load_sp<P>(F(a.b), cb, s, Ns, bb);
+        store_sp<P>(F(a.out), cb, s, Ns, y);
+      } else if constexpr (EPI == E_M_XPAY) {
+        R y[24];
+        load_sp<P>(F(a.y), cb, s, Ns, y);
 #pragma unroll
-      for (int c = 0; c < 24; ++c) {
-        bb[c] -= y[c] + acc[c];
-        part += bb[c] * bb[c];
+        for (int c = 0; c < 24; ++c) y[c] += acc[c];
+        store_sp<P>(F(a.out), cb, s, Ns, y);
+      } else if constexpr (EPI == E_CG_UPDATE) {
+        // alpha = (r, r) / (p, A p) was formed once by the reduction that produced (p, A p)
+        R alpha;
+        if constexpr (P == P_F64) alpha = sc_->alpha;
+        else alpha = sc_->alpha_f;
+        if constexpr (!T::HALF) {
+          // chunk by chunk: four operands of 16 bytes live at a time, not 4 x 24 reals
+          constexpr int RPC = T::RPC;
+#pragma unroll
+          for (int k = 0; k < T::NCH; ++k) {
+            R y[RPC], r[RPC], xx[RPC], pp[RPC];
+            load_chunk<P>(F(a.y), cb, s, Ns, k, y);
+            load_chunk<P>(F(a.r), cb, s, Ns, k, r);
+            load_chunk<P>(F(a.x), cb, s, Ns, k, xx);
+            load_chunk<P>(F(a.p), cb, s, Ns, k, pp);
+#pragma unroll
+            for (int j = 0; j < RPC; ++j) {
+              const R ap = y[j] + acc[k * RPC + j];
+              r[j] -= alpha * ap;
+              xx[j] += alpha * pp[j];
+              part += r[j] * r[j];
+            }
+            store_chunk<P>(F(a.r), cb, s, Ns, k, r);
+            store_chunk<P>(F(a.x), cb, s, Ns, k, xx);
+          }
+        } else {
+          R y[24], r[24], xx[24], pp[24];
+          load_sp<P>(F(a.y), cb, s, Ns, y);
+          load_sp<P>(F(a.r), cb, s, Ns, r);
+          load_sp<P>(F(a.x), cb, s, Ns, xx);
+          load_sp<P>(F(a.p), cb, s, Ns, pp);
+#pragma unroll
+          for (int c = 0; c < 24; ++c) {
+            const R ap = y[c] + acc[c];
+            r[c] -= alpha * ap;
+            xx[c] += alpha * pp[c];
+            part += r[c] * r[c];
+          }
+          store_sp<P>(F(a.r), cb, s, Ns, r);
+          store_sp<P>(F(a.x), cb, s, Ns, xx);
+        }
+      } else if constexpr (EPI == E_RESID) {
+        R y[24], bb[24];
+        load_sp<P>(F(a.y), cb, s, Ns, y);
+        load_sp<P>(F(a.b), cb, s, Ns, bb);
+#pragma unroll
+        for (int c = 0; c < 24; ++c) {
+          bb[c] -= y[c] + acc[c];
+          part += bb[c] * bb[c];
+        }
+        store_sp<P>(F(a.out), cb, s, Ns, bb);
       }
-      store_sp<P>(F(a.out), cb, s, Ns, bb);
     }
   }
   if constexpr (E::has_red) grid_sum<R>(part, a.partials + rb * a.part_stride, a.ticket + rb, a.fin, sc_);

@@ -37,7 +37,7 @@ inline int vec_grid(long n, int sm_count) {
 template <int P, int EPI, int NSC>
 cudaError_t hop_go(const HopArgs &a, cudaStream_t st) {
   const int spb = hop_sites_per_block(P, a.Ns);
-  const size_t smem = hop_smem_bytes<P>(spb, a.Ns, EpiT<EPI>::has_m);
+  const size_t smem = hop_smem_bytes<P, EPI>(spb, a.Ns);
   static std::atomic<size_t> configured{0};  // launches may come from several host threads
   if (smem > 48 * 1024 && configured.load() < smem) {
     cudaError_t e =
@@ -45,8 +45,32 @@ cudaError_t hop_go(const HopArgs &a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     configured.store(smem);
   }
-  const long nblk = (a.h + spb - 1) / spb;
-  k_hop<P, EPI, NSC><<<dim3((unsigned)nblk, a.nrhs > 1 ? a.nrhs : 1), dim3(a.Ns, spb), smem, st>>>(a);
+  const int nrhs = a.nrhs > 1 ? a.nrhs : 1;
+  const long ntile = (a.h + spb - 1) / spb;
+  long nblk = ntile;  // one tile per CTA
+  if constexpr (hop_persistent<EPI>()) {
+    // persistent grid: as many CTAs as are resident at once (shared among the right-hand
+    // sides of a batch), each taking an equal number of tiles
+    const int nthr = a.Ns * spb;
+    const unsigned long long key = ((unsigned long long)smem << 20) | (unsigned long long)nthr;
+    static std::atomic<unsigned long long> cached_key{0};
+    static std::atomic<long> cached_res{0};
+    long res = cached_key.load() == key ? cached_res.load() : 0;
+    if (res <= 0) {
+      int dev = 0, sms = 0, per = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hop<P, EPI, NSC>, nthr, smem);
+      if (e != cudaSuccess) return e;
+      res = (long)std::max(per, 1) * sms;
+      cached_res.store(res);
+      cached_key.store(key);
+    }
+    const long slots = std::max(1L, res / nrhs);
+    const long per_cta = (ntile + slots - 1) / slots;
+    nblk = (ntile + per_cta - 1) / per_cta;
+  }
+  k_hop<P, EPI, NSC><<<dim3((unsigned)nblk, nrhs), dim3(a.Ns, spb), smem, st>>>(a);
   return cudaGetLastError();
 }
 
