@@ -501,8 +501,8 @@ def main():
     n = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2 * NS
     S = {0: 192, 1: 96, 2: 52, 3: 52}[prec]
     G = {0: 144, 1: 72, 2: 24, 3: 24}[prec]
-    alg = {"hop_m5": 2 * S + 8 * G / NS, "hop_xpay": 3 * S + 8 * G / NS, "hop_update": 7 * S + 8 * G / NS,
-           "smix_p": 4 * S}
+    alg = {"hop_m5": 2 * S + 8 * G / NS, "hop_xpay": 3 * S + 8 * G / NS, "hop_update": 4 * S + 8 * G / NS,
+           "smix_p": 6 * S}
     cls_ms = {k: sum(p["class_ms"][k] for p in prof) for k in dwf.KC_NAMES}
     cls_n = {k: sum(p["class_launches"][k] for p in prof) for k in dwf.KC_NAMES}
     total = sum(cls_ms.values())

@@ -885,6 +885,7 @@ dwf_status cg_iteration(dwf_ctx *c, cudaStream_t st, const SolveState &S, const 
     m.out = S.w;
     m.r = S.r;
     m.p = S.p;
+    m.x = S.x;
     m.K = dmat(c, P, MK_M5T);
     m.K2 = dmat(c, P, MK_ID);
     m.coef = 1.0;
@@ -927,8 +928,6 @@ dwf_status cg_iteration(dwf_ctx *c, cudaStream_t st, const SolveState &S, const 
   e.in = S.u;
   e.y = S.q;
   e.r = S.r;
-  e.x = S.x;
-  e.p = S.p;
   e.K = dmat(c, P, MK_M5);
   e.coef = 0.5;
   e.fin = FIN_CG;
@@ -939,8 +938,8 @@ dwf_status cg_iteration(dwf_ctx *c, cudaStream_t st, const SolveState &S, const 
 }
 
 // FP64 restart of right-hand side k (Algorithm 2), with the context pointed at its slot:
-// x_hat += x, x = 0, r_hat = b - C C^dag x_hat, |r_hat|^2 -> red, r = r_hat in the inner
-// precision, |r|^2 -> red2
+// x_hat += x + alpha p (the last inner step, which the skipped p-update did not add), x = 0,
+// r_hat = b - C C^dag x_hat, |r_hat|^2 -> red, r = r_hat in the inner precision, |r|^2 -> red2
 dwf_status fp64_restart(dwf_ctx *c, cudaStream_t st, const SolveState &S, int k) {
   const Field xh = at(c, S.xh, k, P_F64), rh = at(c, S.rh, k, P_F64), bk = at(c, S.b, k, P_F64);
   const Field x = at(c, S.x, k, S.prec), r = at(c, S.r, k, S.prec);
@@ -949,6 +948,8 @@ dwf_status fp64_restart(dwf_ctx *c, cudaStream_t st, const SolveState &S, int k)
     memset(&v, 0, sizeof(v));
     v.a = xh;
     v.b = x;
+    v.c = at(c, S.p, k, S.prec);
+    v.sc = c->d_sc;
     v.n = c->h * c->Ns;
     v.Ns = c->Ns;
     Timed t(c, st, DWF_KC_F64);
@@ -1093,6 +1094,8 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
       h.beta = reset_p ? 0.0 : rr_conv / h.rr_old;
     }
     h.beta_f = (float)h.beta;
+    h.alpha = 0.0;  // no inner step pending: x = 0 (the restart added the last one)
+    h.alpha_f = 0.0f;
     h.rr = rr_conv;
     h.rmax2 = rr_conv;
     h.rr_start = rr_conv;

@@ -180,7 +180,7 @@ enum {
   E_XPAY_G5 = 2,   // out = y + coef g5 H, |out|^2 -> fin
   E_XPAY = 3,      // out = y + coef H
   E_M_XPAY = 4,    // out = y + K H
-  E_CG_UPDATE = 5, // Ap = y + K H; r -= alpha Ap; x += alpha p; |r|^2 -> FIN_CG
+  E_CG_UPDATE = 5, // Ap = y + K H; r -= alpha Ap; |r|^2 -> FIN_CG
   E_RESID = 6      // out = b - (y + K H), |out|^2 -> fin
 };
 
@@ -190,7 +190,7 @@ template <int EPI> struct EpiT {
 };
 
 struct HopArgs {
-  Field in, out, y, b, r, x, p;
+  Field in, out, y, b, r;
   const void *gauge;   // doubled gauge of the output parity: [cb][8][LREALS]
   const int *nbr;      // [cb][8] for the output parity
   const void *K;       // matrix along s in kernel order K[chi][t][s] (precision real)
@@ -321,11 +321,7 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
     const size_t off = (size_t)c0 * T::NCH * Ns * 16;
     if constexpr (EPI == E_XPAY_G5 || EPI == E_XPAY || EPI == E_M_XPAY || EPI == E_CG_UPDATE || EPI == E_RESID)
       prefetch_l2(static_cast<const unsigned char *>(F(a.y).v) + off, ob);
-    if constexpr (EPI == E_CG_UPDATE) {
-      prefetch_l2(static_cast<const unsigned char *>(F(a.r).v) + off, ob);
-      prefetch_l2(static_cast<const unsigned char *>(F(a.x).v) + off, ob);
-      prefetch_l2(static_cast<const unsigned char *>(F(a.p).v) + off, ob);
-    }
+    if constexpr (EPI == E_CG_UPDATE) prefetch_l2(static_cast<const unsigned char *>(F(a.r).v) + off, ob);
     if constexpr (EPI == E_RESID) prefetch_l2(static_cast<const unsigned char *>(F(a.b).v) + off, ob);
   };
 
@@ -534,41 +530,32 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
         R alpha;
         if constexpr (P == P_F64) alpha = sc_->alpha;
         else alpha = sc_->alpha_f;
+        // (x += alpha p is deferred to the next iteration's p-update, which reads p anyway)
         if constexpr (!T::HALF) {
-          // chunk by chunk: four operands of 16 bytes live at a time, not 4 x 24 reals
+          // chunk by chunk: two operands of 16 bytes live at a time, not 2 x 24 reals
           constexpr int RPC = T::RPC;
 #pragma unroll
           for (int k = 0; k < T::NCH; ++k) {
-            R y[RPC], r[RPC], xx[RPC], pp[RPC];
+            R y[RPC], r[RPC];
             load_chunk<P>(F(a.y), cb, s, Ns, k, y);
             load_chunk<P>(F(a.r), cb, s, Ns, k, r);
-            load_chunk<P>(F(a.x), cb, s, Ns, k, xx);
-            load_chunk<P>(F(a.p), cb, s, Ns, k, pp);
 #pragma unroll
             for (int j = 0; j < RPC; ++j) {
-              const R ap = y[j] + acc[k * RPC + j];
-              r[j] -= alpha * ap;
-              xx[j] += alpha * pp[j];
+              r[j] -= alpha * (y[j] + acc[k * RPC + j]);
               part += r[j] * r[j];
             }
             store_chunk<P>(F(a.r), cb, s, Ns, k, r);
-            store_chunk<P>(F(a.x), cb, s, Ns, k, xx);
           }
         } else {
-          R y[24], r[24], xx[24], pp[24];
+          R y[24], r[24];
           load_sp<P>(F(a.y), cb, s, Ns, y);
           load_sp<P>(F(a.r), cb, s, Ns, r);
-          load_sp<P>(F(a.x), cb, s, Ns, xx);
-          load_sp<P>(F(a.p), cb, s, Ns, pp);
 #pragma unroll
           for (int c = 0; c < 24; ++c) {
-            const R ap = y[c] + acc[c];
-            r[c] -= alpha * ap;
-            xx[c] += alpha * pp[c];
+            r[c] -= alpha * (y[c] + acc[c]);
             part += r[c] * r[c];
           }
           store_sp<P>(F(a.r), cb, s, Ns, r);
-          store_sp<P>(F(a.x), cb, s, Ns, xx);
         }
       } else if constexpr (EPI == E_RESID) {
         R y[24], bb[24];
@@ -591,12 +578,12 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
 enum {
   S_PLAIN = 0,  // out = K in
   S_G5 = 1,     // out = K g5 in
-  S_CGP = 2,    // p = r + beta p (stored); out = K g5 p
+  S_CGP = 2,    // x += alpha p, then p = r + beta p (both stored); out = K g5 p
   S_DUAL = 3    // out = K in; out2 = K2 in
 };
 
 struct SmixArgs {
-  Field in, out, out2, r, p;
+  Field in, out, out2, r, p, x;
   const void *K, *K2;  // K[chi][t][s]
   double coef;
   long h;
@@ -642,12 +629,26 @@ __global__ void __launch_bounds__(256) k_smix(const SmixArgs a) {
   R v[24];
   if (active) {
     if constexpr (MODE == S_CGP) {
-      R r[24];
-      R beta;
-      if constexpr (P == P_F64) beta = sc_->beta;
-      else beta = sc_->beta_f;
-      load_sp<P>(F(a.r), cb, s, Ns, r);
+      // Algorithm 1: the previous iteration's x += alpha p (alpha is still that iteration's;
+      // 0 after a restart, which adds the pending step itself), then p = r + beta p
+      R beta, alpha;
+      if constexpr (P == P_F64) {
+        beta = sc_->beta;
+        alpha = sc_->alpha;
+      } else {
+        beta = sc_->beta_f;
+        alpha = sc_->alpha_f;
+      }
       load_sp<P>(F(a.p), cb, s, Ns, v);
+      {
+        R xx[24];
+        load_sp<P>(F(a.x), cb, s, Ns, xx);
+#pragma unroll
+        for (int c = 0; c < 24; ++c) xx[c] += alpha * v[c];
+        store_sp<P>(F(a.x), cb, s, Ns, xx);
+      }
+      R r[24];
+      load_sp<P>(F(a.r), cb, s, Ns, r);
 #pragma unroll
       for (int c = 0; c < 24; ++c) v[c] = r[c] + beta * v[c];
       store_sp<P>(F(a.p), cb, s, Ns, v);
@@ -726,16 +727,30 @@ __global__ void __launch_bounds__(256) k_convert(const VecArgs v) {
   }
 }
 
-// FP64 a += (precision P) b; b = 0  (x_hat += x at a restart, Algorithm 2)
+// FP64 a += (precision P) (b + alpha c); b = 0  (x_hat += x at a restart, Algorithm 2, with
+// the CG step x += alpha p of the last inner iteration, deferred to a p-update that did not
+// run, added first; c may be absent)
 template <int P>
 __global__ void __launch_bounds__(256) k_accum(const VecArgs v) {
+  using R = typename PT<P>::real;
+  R alpha = 0;
+  if (v.c.v) {
+    if constexpr (P == P_F64) alpha = v.sc->alpha;
+    else alpha = v.sc->alpha_f;
+  }
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < v.n; i += (long)gridDim.x * blockDim.x) {
     const long cb = i / v.Ns;
     const int s = (int)(i % v.Ns);
     double xa[24];
-    typename PT<P>::real xb[24];
+    R xb[24];
     load_sp<P_F64>(v.a, cb, s, v.Ns, xa);
     load_sp<P>(v.b, cb, s, v.Ns, xb);
+    if (v.c.v) {
+      R pc[24];
+      load_sp<P>(v.c, cb, s, v.Ns, pc);
+#pragma unroll
+      for (int c = 0; c < 24; ++c) xb[c] += alpha * pc[c];
+    }
 #pragma unroll
     for (int c = 0; c < 24; ++c) { xa[c] += (double)xb[c]; xb[c] = 0; }
     store_sp<P_F64>(v.a, cb, s, v.Ns, xa);
