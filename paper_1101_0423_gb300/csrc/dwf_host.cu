@@ -153,6 +153,103 @@ bool build_matrices(dwf_ctx *c) {
   return true;
 }
 
+// M5 and M5^T of Eq. 8 as recurrences along s, for the hop epilogues.  With
+// A = (d - m0) sqrt(omega) (1 + cL) + omega^{-1/2} (1 - L) (cyclic bidiagonal through the
+// corner kappa of L, Eq. 4) and P = sqrt(omega) (1 + cL): M5 = P A^{-1}, M5^T = A^{-T} P^T.
+// A chirality's recurrence visits s in one direction (step j at s = j, or Ns - 1 - j when
+// backward: chirality - for M5, chirality + for M5^T); every step uses the values of the
+// step before it, and step 0 those of the last step scaled by kappa:
+//   g_j = PS_j v_j + PN_j vp,  z_j = (g_j - BB_j zp) AI_j,  u_j = QS_j z_j + QN_j zp,
+// with the first zp = kappa z_last from the closure z_last = sum_j W_j v_j and the first
+// vp = kappa v_last.  Table: per chirality, RC_N reals per step.
+enum { RC_PS, RC_PN, RC_BB, RC_AI, RC_QS, RC_QN, RC_W, RC_N = 8 };
+
+void apply_recurrence(const double *T, int Ns, bool bwd, double kappa, const double *v, double *u) {
+  auto sg = [&](int j) { return bwd ? Ns - 1 - j : j; };
+  double zc = 0.0;
+  for (int j = 0; j < Ns; ++j) zc += T[j * RC_N + RC_W] * v[sg(j)];
+  double zp = kappa * zc, vp = kappa * v[sg(Ns - 1)];
+  for (int j = 0; j < Ns; ++j) {
+    const double *t = T + j * RC_N;
+    const int s = sg(j);
+    const double g = t[RC_PS] * v[s] + t[RC_PN] * vp;
+    const double z = (g - t[RC_BB] * zp) * t[RC_AI];
+    u[s] = t[RC_QS] * z + t[RC_QN] * zp;
+    zp = z;
+    vp = v[s];
+  }
+}
+
+// builds the tables and checks each against the dense M5 / M5^T column by column
+bool build_recurrences(dwf_ctx *c) {
+  const int Ns = c->Ns;
+  const double kappa = -c->mq / (2.0 * c->m0);
+  const double dm = kD - c->m0;
+  std::vector<double> a(Ns), beta(Ns), sw(Ns), cc(Ns), lam(Ns), u(Ns), v(Ns);
+  for (int s = 0; s < Ns; ++s) {
+    sw[s] = sqrt(c->omega[s]);
+    a[s] = dm * sw[s] + 1.0 / sw[s];
+    beta[s] = dm * c->sigma[s] / sw[s] - 1.0 / sw[s];
+    cc[s] = c->sigma[s] / c->omega[s];
+  }
+  for (int tr = 0; tr < 2; ++tr) {
+    c->rec[tr].assign((size_t)2 * Ns * RC_N, 0.0);
+    for (int chi = 0; chi < 2; ++chi) {
+      const bool bwd = (chi ^ tr) != 0;
+      auto sg = [&](int j) { return bwd ? Ns - 1 - j : j; };
+      double *T = c->rec[tr].data() + (size_t)chi * Ns * RC_N;
+      for (int j = 0; j < Ns; ++j) {
+        const int s = sg(j), n = sg((j + Ns - 1) % Ns);  // this step's s and the step before's
+        double *t = T + j * RC_N;
+        if (a[s] == 0.0) return false;
+        t[RC_AI] = 1.0 / a[s];
+        if (tr == 0) {  // M5 = P A^{-1}: solve, then u = sqrt(omega) (z + c L z)
+          t[RC_PS] = 1.0;
+          t[RC_PN] = 0.0;
+          t[RC_BB] = beta[s];
+          t[RC_QS] = sw[s];
+          t[RC_QN] = sw[s] * cc[s];
+        } else {  // M5^T = A^{-T} P^T: g = P^T v, then solve with A^T
+          t[RC_PS] = sw[s];
+          t[RC_PN] = sw[n] * cc[n];
+          t[RC_BB] = beta[n];
+          t[RC_QS] = 1.0;
+          t[RC_QN] = 0.0;
+        }
+      }
+      // closure: z_last = sum_j lam_j g_j (forward substitution with z depending linearly on
+      // z_last through step 0), and g_j = PS_j v_j + PN_j vp_j gives the weights on v
+      double q = -T[RC_BB] * kappa * T[RC_AI];
+      for (int j = 1; j < Ns; ++j) q = -T[j * RC_N + RC_BB] * q * T[j * RC_N + RC_AI];
+      const double den = 1.0 - q;
+      if (den == 0.0) return false;
+      double r = 1.0;
+      for (int j = Ns - 1; j >= 0; --j) {
+        lam[j] = T[j * RC_N + RC_AI] * r / den;
+        r *= -T[j * RC_N + RC_BB] * T[j * RC_N + RC_AI];
+      }
+      for (int j = 0; j < Ns; ++j) {
+        double w = lam[j] * T[j * RC_N + RC_PS];
+        if (j + 1 < Ns) w += lam[j + 1] * T[(j + 1) * RC_N + RC_PN];
+        if (j == Ns - 1) w += kappa * lam[0] * T[RC_PN];
+        T[j * RC_N + RC_W] = w;
+      }
+      // check: the recurrence reproduces every column of the dense matrix
+      const double *M = c->mat[tr ? MK_M5T : MK_M5].data() + (size_t)chi * Ns * Ns;
+      double mmax = 0.0;
+      for (int i = 0; i < Ns * Ns; ++i) mmax = std::max(mmax, fabs(M[i]));
+      for (int t0 = 0; t0 < Ns; ++t0) {
+        std::fill(v.begin(), v.end(), 0.0);
+        v[t0] = 1.0;
+        apply_recurrence(T, Ns, bwd, kappa, v.data(), u.data());
+        for (int s = 0; s < Ns; ++s)
+          if (!(fabs(u[s] - M[s * Ns + t0]) <= 1e-11 * mmax)) return false;
+      }
+    }
+  }
+  return true;
+}
+
 // ------------------------------------------------------------------ buffers
 
 dwf_status get_buf(dwf_ctx *c, const std::string &name, int prec, Field *f) {
@@ -340,6 +437,15 @@ dwf_status hop(dwf_ctx *c, cudaStream_t st, int prec, int epi, HopArgs a, int cl
 
 const void *dmat(dwf_ctx *c, int prec, int kind) { return c->dmat[mat_index(prec)][kind]; }
 
+// the hop epilogue's matrix along s, M5 or M5^T: dense (FP32 arithmetic) and as a
+// recurrence table (FP64)
+void set_m5(HopArgs &a, dwf_ctx *c, int prec, bool trans) {
+  a.K = dmat(c, prec, trans ? MK_M5T : MK_M5);
+  a.rec = c->drec[mat_index(prec)][trans ? 1 : 0];
+  a.mtrans = trans ? 1 : 0;
+  a.kappa = -c->mq / (2.0 * c->m0);
+}
+
 dwf_status smix(dwf_ctx *c, cudaStream_t st, int prec, int mode, Field in, Field out, int kind,
                 double coef, int cls, Field out2 = Field{nullptr, nullptr}, int kind2 = MK_ID,
                 Field r = Field{nullptr, nullptr}, Field p = Field{nullptr, nullptr}, int use_flag = 0) {
@@ -427,7 +533,7 @@ dwf_status op_cdag(dwf_ctx *c, cudaStream_t st, int prec, int sp, Field v, Field
   HopArgs a = hop_args(c, prec, op);
   a.in = w;
   a.out = t;
-  a.K = dmat(c, prec, MK_M5T);
+  set_m5(a, c, prec, true);
   a.coef = -0.5;
   TRY(hop(c, st, prec, E_M, a, cls));
   HopArgs b = hop_args(c, prec, sp);
@@ -445,14 +551,14 @@ dwf_status op_c(dwf_ctx *c, cudaStream_t st, int prec, int sp, Field v, Field ou
   HopArgs a = hop_args(c, prec, op);
   a.in = v;
   a.out = u;
-  a.K = dmat(c, prec, MK_M5);
+  set_m5(a, c, prec, false);
   a.coef = -0.5;
   TRY(hop(c, st, prec, E_M, a, cls));
   HopArgs b = hop_args(c, prec, sp);
   b.in = u;
   b.y = v;
   b.out = out;
-  b.K = dmat(c, prec, MK_M5);
+  set_m5(b, c, prec, false);
   b.coef = 0.5;
   TRY(hop(c, st, prec, E_M_XPAY, b, cls));
   return DWF_OK;
@@ -553,7 +659,7 @@ dwf_status dwf_create(const int dims[4], int Ns, double m0, double mq, const dou
   c->mq = mq;
   c->omega.assign(omega, omega + Ns);
   c->sigma.assign(sigma, sigma + Ns);
-  if (!build_matrices(c)) {
+  if (!build_matrices(c) || !build_recurrences(c)) {
     delete c;
     return DWF_EINVAL;
   }
@@ -585,6 +691,17 @@ dwf_status dwf_create(const int dims[4], int Ns, double m0, double mq, const dou
     if ((e = cudaMemcpy(c->dmat[1][k], kf.data(), nm * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
       return bail(e);
   }
+  for (int tr = 0; tr < 2; ++tr) {
+    const size_t nr = c->rec[tr].size();
+    std::vector<float> rf(c->rec[tr].begin(), c->rec[tr].end());
+    if ((e = cudaMalloc(&c->drec[0][tr], nr * sizeof(double))) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&c->drec[1][tr], nr * sizeof(float))) != cudaSuccess) return bail(e);
+    if ((e = cudaMemcpy(c->drec[0][tr], c->rec[tr].data(), nr * sizeof(double), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return bail(e);
+    if ((e = cudaMemcpy(c->drec[1][tr], rf.data(), nr * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(e);
+  }
   Geom g = geom(c);
   for (int p = 0; p < 2; ++p) {
     if ((e = cudaMalloc((void **)&c->d_nbr[p], (size_t)c->h * 8 * sizeof(int))) != cudaSuccess) return bail(e);
@@ -614,6 +731,9 @@ dwf_status dwf_destroy(dwf_ctx *c) {
     if (kv.second.nrm) cudaFree(kv.second.nrm);
   }
   for (auto &row : c->dmat)
+    for (void *p : row)
+      if (p) cudaFree(p);
+  for (auto &row : c->drec)
     for (void *p : row)
       if (p) cudaFree(p);
   for (auto &row : c->d_gauge)
@@ -902,7 +1022,7 @@ dwf_status cg_iteration(dwf_ctx *c, cudaStream_t st, const SolveState &S, const 
   HopArgs a = hop_args(c, P, S.op);
   a.in = S.w;
   a.out = S.t;
-  a.K = dmat(c, P, MK_M5T);
+  set_m5(a, c, P, true);
   a.coef = -0.5;
   a.use_flag = 1;
   batch(a);
@@ -919,7 +1039,7 @@ dwf_status cg_iteration(dwf_ctx *c, cudaStream_t st, const SolveState &S, const 
   HopArgs d = hop_args(c, P, S.op);
   d.in = S.q;
   d.out = S.u;
-  d.K = dmat(c, P, MK_M5);
+  set_m5(d, c, P, false);
   d.coef = -0.5;
   d.use_flag = 1;
   batch(d);
@@ -928,7 +1048,7 @@ dwf_status cg_iteration(dwf_ctx *c, cudaStream_t st, const SolveState &S, const 
   e.in = S.u;
   e.y = S.q;
   e.r = S.r;
-  e.K = dmat(c, P, MK_M5);
+  set_m5(e, c, P, false);
   e.coef = 0.5;
   e.fin = FIN_CG;
   e.use_flag = 1;
@@ -959,7 +1079,7 @@ dwf_status fp64_restart(dwf_ctx *c, cudaStream_t st, const SolveState &S, int k)
   HopArgs a = hop_args(c, P_F64, S.op);
   a.in = S.w64;
   a.out = S.t64;
-  a.K = dmat(c, P_F64, MK_M5T);
+  set_m5(a, c, P_F64, true);
   a.coef = -0.5;
   TRY(hop(c, st, P_F64, E_M, a, DWF_KC_F64));
   HopArgs b = hop_args(c, P_F64, S.sp);
@@ -972,7 +1092,7 @@ dwf_status fp64_restart(dwf_ctx *c, cudaStream_t st, const SolveState &S, int k)
   HopArgs d = hop_args(c, P_F64, S.op);
   d.in = S.q64;
   d.out = S.u64;
-  d.K = dmat(c, P_F64, MK_M5);
+  set_m5(d, c, P_F64, false);
   d.coef = -0.5;
   TRY(hop(c, st, P_F64, E_M, d, DWF_KC_F64));
   HopArgs e = hop_args(c, P_F64, S.sp);
@@ -980,7 +1100,7 @@ dwf_status fp64_restart(dwf_ctx *c, cudaStream_t st, const SolveState &S, int k)
   e.y = S.q64;
   e.b = bk;
   e.out = rh;
-  e.K = dmat(c, P_F64, MK_M5);
+  set_m5(e, c, P_F64, false);
   e.coef = 0.5;
   e.fin = FIN_RED;
   TRY(hop(c, st, P_F64, E_RESID, e, DWF_KC_F64));
@@ -1126,7 +1246,7 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
       a.in = etap[S.op];
       a.y = etap[S.sp];
       a.out = bk;
-      a.K = dmat(c, P_F64, MK_M5);
+      set_m5(a, c, P_F64, false);
       a.coef = 0.5;
       TRY(hop(c, st, P_F64, E_M_XPAY, a, DWF_KC_F64));
     } else {
@@ -1264,7 +1384,7 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
     a.in = phi[S.sp];
     a.y = etap[S.op];
     a.out = phi[S.op];
-    a.K = dmat(c, P_F64, MK_M5);
+    set_m5(a, c, P_F64, false);
     a.coef = 0.5;
     TRY(hop(c, st, P_F64, E_M_XPAY, a, DWF_KC_F64));
     for (int p = 0; p < 2; ++p) {

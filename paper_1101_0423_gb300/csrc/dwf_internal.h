@@ -39,6 +39,9 @@ struct dwf_ctx {
   std::vector<double> mat[dwf::MK_COUNT];
   // device matrices per arithmetic precision (0: double, 1: float), kernel order
   void *dmat[2][dwf::MK_COUNT] = {};
+  // M5 (0) and M5^T (1) as recurrence tables along s (host FP64; device per precision)
+  std::vector<double> rec[2];
+  void *drec[2][2] = {};
   int *d_nbr[2] = {nullptr, nullptr};
   double *d_U = nullptr;  // FP64 host-layout copy of the gauge field
   void *d_gauge[4][2] = {};

@@ -193,8 +193,12 @@ struct HopArgs {
   Field in, out, y, b, r;
   const void *gauge;   // doubled gauge of the output parity: [cb][8][LREALS]
   const int *nbr;      // [cb][8] for the output parity
-  const void *K;       // matrix along s in kernel order K[chi][t][s] (precision real)
-  double coef;         // scale of H (plain/xpay) or of K (matrix epilogues)
+  const void *K;       // FP32 arithmetic: M5 or M5^T, dense, kernel order K[chi][t][s]
+  const void *rec;     // FP64: the same as a recurrence table along s, per chirality Ns
+                       // steps of {PS, PN, BB, AI, QS, QN, W, 0}
+  int mtrans;          // 0: M5, 1: M5^T (direction of each chirality's recurrence)
+  double kappa;        // corner of L, -mq / (2 m0) (Eq. 4)
+  double coef;         // scale of H (plain/xpay) or of the matrix (M5 epilogues)
   long h;              // sites per parity
   int Ns;
   int fin;             // FIN_* of the reduction
@@ -226,12 +230,12 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(
 // dynamic shared memory of k_hop, in bytes:
 //   [mbarrier, 64 B][links as copied][neighbour indices][links packed for f32x2][stage][K]
 // FP32-arithmetic kernels (F32, fp16, bf16) expand each tile's links into nine 16-byte
-// entries (wr, wr, -wi, wi) -- the 16-bit forms rebuild their third row there -- and keep K
-// duplicated as (k, k) pairs; FP64 kernels use the links as copied.
+// entries (wr, wr, -wi, wi) -- the 16-bit forms rebuild their third row there; FP64 kernels
+// use the links as copied.
 //
 // Layout: mbarriers; `nb` buffers of raw links and of neighbour indices (filled by TMA bulk
 // copies: two when a persistent CTA receives the next tile while computing this one); the
-// tile's expanded links; K.  The M5 staging rows overlay the link buffers from the start
+// tile's expanded links; M5.  The M5 staging rows overlay the link buffers from the start
 // (kernels with an M5 epilogue take one tile per CTA, so all of them are dead by then).
 // Shared memory is kept small on purpose: what the CTAs leave of the SM's 256 KB is the L1
 // that holds the neighbour gathers in flight.
@@ -257,8 +261,11 @@ template <int P> struct HopSmem {
     const size_t st = has_m ? 64 + stage(spb, Ns) : 0;
     return align16(e > st ? e : st);
   }
+  // M5 / M5^T: dense as (k, k) pairs (FP32 arithmetic) or a recurrence table of
+  // 2 chiralities x Ns steps x 8 reals (FP64)
   __host__ __device__ static size_t bytes(int spb, int Ns, int nb, bool has_m) {
-    return off_k(spb, Ns, nb, has_m) + (has_m ? align16((size_t)2 * Ns * Ns * (F2 ? 8 : sizeof(double))) : 0);
+    return off_k(spb, Ns, nb, has_m) +
+           (has_m ? align16(F2 ? (size_t)2 * Ns * Ns * 8 : (size_t)2 * Ns * 8 * sizeof(RL)) : 0);
   }
 };
 // kernels without an M5 epilogue run persistent CTAs (measured: hop_xpay 96 -> 79 us); the
@@ -338,9 +345,13 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
         sK2[i] = make_float2(k, k);
       }
     } else {
-      const double *Kg = static_cast<const double *>(a.K);
-      double *sKd = reinterpret_cast<double *>(sKb);
-      for (int i = tid; i < 2 * Ns * Ns; i += nthr) sKd[i] = a.coef * Kg[i];
+      // the matrix acts on coef H: coef scales g and the closure (entries PS, PN, W)
+      const R *Tg = static_cast<const R *>(a.rec);
+      R *sT = reinterpret_cast<R *>(sKb);
+      for (int i = tid; i < 2 * Ns * 8; i += nthr) {
+        const int e = i & 7;
+        sT[i] = (e == 0 || e == 1 || e == 6) ? (R)(a.coef * (double)Tg[i]) : Tg[i];
+      }
     }
   }
   __syncthreads();
@@ -452,9 +463,9 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
     }
 
     if constexpr (E::has_m) {
-      // M5-type epilogue (Sec. 3.3): out_s = sum_t K_{st} H_t per chirality; the Ns slices
-      // of a site are in this CTA, staged through shared memory (rows and sites padded by
-      // 16 bytes against bank conflicts; the stage overlays the link buffers)
+      // M5-type epilogue (Sec. 3.3): out_s = sum_t (M5)_{st} H_t per chirality; the Ns
+      // slices of a site are in this CTA, staged through shared memory (rows and sites padded
+      // by 16 bytes against bank conflicts; the stage overlays the link buffers)
       R *sB = reinterpret_cast<R *>(sS);
       constexpr int ROW = SM::ROW;
       const int sstride = Ns * ROW + 16 / (int)sizeof(R);
@@ -463,9 +474,11 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
 #pragma unroll
       for (int c = 0; c < 24; ++c) mine[c] = acc[c];
       __syncthreads();
-      if (active) {
-        const R *site = sB + (size_t)sl * sstride;
-        if constexpr (F2) {
+      if constexpr (F2) {
+        // FP32 arithmetic: dense, every (site, s) thread forms its own output row from the
+        // site's Ns staged rows (independent sums: latency is what limits these kernels)
+        if (active) {
+          const R *site = sB + (size_t)sl * sstride;
           const f2 *sK2 = reinterpret_cast<const f2 *>(sKb);
           f2 o[12];
 #pragma unroll
@@ -485,19 +498,72 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
           }
 #pragma unroll
           for (int q = 0; q < 12; ++q) upk2(o[q], acc[2 * q], acc[2 * q + 1]);
-        } else {
-          const double *sKd = reinterpret_cast<const double *>(sKb);
+        }
+      } else {
+        // FP64: M5 (or M5^T) along s, Eq. 8, as a recurrence, which halves the FP64
+        // operations that limit these kernels: one 16-byte column (two reals of one
+        // chirality) of one site per item; a closure sweep, then the sweep that overwrites
+        // the column with the result (the item owns its column)
+        {
+          constexpr int CW = 2, NCK = 12;
+          using V = double2;
+          const R kap = (R)a.kappa;
+          const R *sT = reinterpret_cast<const R *>(sKb);
+          for (int item = tid; item < nsite * NCK; item += nthr) {
+            const int l = item / NCK, k = item - l * NCK;
+            const int chi = k >= NCK / 2 ? 1 : 0;
+            const bool bwd = (chi ^ a.mtrans) != 0;
+            const R *Tc = sT + chi * Ns * 8;
+            R *col = sB + (size_t)l * sstride + k * CW;
+            R zc[CW], vl[CW];
 #pragma unroll
-          for (int c = 0; c < 24; ++c) acc[c] = 0;
-          for (int t = 0; t < Ns; ++t) {
-            const R kp = sKd[t * Ns + s];
-            const R km = sKd[Ns * Ns + t * Ns + s];
-            const R *v = site + t * ROW;
+            for (int q = 0; q < CW; ++q) zc[q] = 0;
+#pragma unroll 4
+            for (int j = 0; j < Ns; ++j) {
+              const int sj = bwd ? Ns - 1 - j : j;
+              const V w4 = *reinterpret_cast<const V *>(col + sj * ROW);
+              const R *v = reinterpret_cast<const R *>(&w4);
+              const R w = Tc[j * 8 + 6];
 #pragma unroll
-            for (int c = 0; c < 12; ++c) acc[c] += kp * v[c];
+              for (int q = 0; q < CW; ++q) {
+                zc[q] += w * v[q];
+                vl[q] = v[q];
+              }
+            }
+            R zp[CW], vp[CW];
 #pragma unroll
-            for (int c = 12; c < 24; ++c) acc[c] += km * v[c];
+            for (int q = 0; q < CW; ++q) {
+              zp[q] = kap * zc[q];
+              vp[q] = kap * vl[q];
+            }
+#pragma unroll 4
+            for (int j = 0; j < Ns; ++j) {
+              const int sj = bwd ? Ns - 1 - j : j;
+              R t[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) t[e] = Tc[j * 8 + e];
+              V *cp = reinterpret_cast<V *>(col + sj * ROW);
+              const V w4 = *cp;
+              const R *v = reinterpret_cast<const R *>(&w4);
+              V o4;
+              R *o = reinterpret_cast<R *>(&o4);
+#pragma unroll
+              for (int q = 0; q < CW; ++q) {
+                const R g = t[0] * v[q] + t[1] * vp[q];
+                const R z = (g - t[2] * zp[q]) * t[3];
+                o[q] = t[4] * z + t[5] * zp[q];
+                zp[q] = z;
+                vp[q] = v[q];
+              }
+              *cp = o4;
+            }
           }
+        }
+        __syncthreads();
+        if (active) {
+          const R *row = sB + (size_t)sl * sstride + (size_t)s * ROW;
+#pragma unroll
+          for (int c = 0; c < 24; ++c) acc[c] = row[c];
         }
       }
     }
