@@ -36,7 +36,8 @@ template <> struct PT<P_F64> {
 };
 template <> struct PT<P_F32> {
   using real = float; using chunk = float4; using lreal = float;
-  static constexpr int NCH = 6, RPC = 4, LREALS = 18; static constexpr bool HALF = false;
+  // links padded to 20 reals (80 bytes) so that the nine complex entries load as five float4
+  static constexpr int NCH = 6, RPC = 4, LREALS = 20; static constexpr bool HALF = false;
 };
 template <> struct PT<P_F16> {
   using real = float; using chunk = uint4; using lreal = __half;
@@ -331,6 +332,56 @@ __device__ __forceinline__ void hop_dir_f2s(f2 (&acc)[12], const f2 (&ps)[12], c
       wh = fma2(B1, hs[j][1], wh);
       wh = fma2(A2, h[j][2], wh);
       wh = fma2(B2, hs[j][2], wh);
+      acc[a + 3 * j] = add2(acc[a + 3 * j], wh);
+      if (ad_col(MU, 0) == j) acc[a + 6] = add_phase_rt<ad_ph(MU, 0)>(acc[a + 6], wh, sg);
+      if (ad_col(MU, 1) == j) acc[a + 9] = add_phase_rt<ad_ph(MU, 1)>(acc[a + 9], wh, sg);
+    }
+  }
+}
+
+// FP32 hop along MU with the link as stored (nine complex entries, 16-byte aligned pairs):
+// W h = P + (-1, 1) (Q.y, Q.x) with P = sum_b W_b (hr_b, hr_b), Q = sum_b W_b (hi_b, hi_b)
+template <int MU>
+__device__ __forceinline__ void hop_dir_raw(f2 (&acc)[12], const f2 (&ps)[12], const float4 *Wl,
+                                            const SignPairs &sg) {
+  f2 hr[2][3], hi[2][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const f2 h0 = add_phase_rt<a_ph(MU, 0)>(ps[a], ps[a + 3 * (2 + a_col(MU, 0))], sg);
+    const f2 h1 = add_phase_rt<a_ph(MU, 1)>(ps[a + 3], ps[a + 3 * (2 + a_col(MU, 1))], sg);
+    float x, y;
+    upk2(h0, x, y);
+    hr[0][a] = pk2(x, x);
+    hi[0][a] = pk2(y, y);
+    upk2(h1, x, y);
+    hr[1][a] = pk2(x, x);
+    hi[1][a] = pk2(y, y);
+  }
+  const f2 sgn = pk2(-1.f, 1.f);
+  float4 w1;  // row 0 ends and row 1 starts in the second float4
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    f2 W0, W1, W2;  // row a: entries 3a, 3a + 1, 3a + 2
+    if (a == 0) {
+      const float4 w0 = Wl[0];
+      w1 = Wl[1];
+      W0 = pk2(w0.x, w0.y), W1 = pk2(w0.z, w0.w), W2 = pk2(w1.x, w1.y);
+    } else if (a == 1) {
+      const float4 w2 = Wl[2];
+      W0 = pk2(w1.z, w1.w), W1 = pk2(w2.x, w2.y), W2 = pk2(w2.z, w2.w);
+    } else {
+      const float4 w3 = Wl[3], w4 = Wl[4];
+      W0 = pk2(w3.x, w3.y), W1 = pk2(w3.z, w3.w), W2 = pk2(w4.x, w4.y);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      f2 P = mul2(W0, hr[j][0]);
+      P = fma2(W1, hr[j][1], P);
+      P = fma2(W2, hr[j][2], P);
+      f2 Q = mul2(W0, hi[j][0]);
+      Q = fma2(W1, hi[j][1], Q);
+      Q = fma2(W2, hi[j][2], Q);
+      const f2 wh = fma2(sgn, swp2(Q), P);
       acc[a + 3 * j] = add2(acc[a + 3 * j], wh);
       if (ad_col(MU, 0) == j) acc[a + 6] = add_phase_rt<ad_ph(MU, 0)>(acc[a + 6], wh, sg);
       if (ad_col(MU, 1) == j) acc[a + 9] = add_phase_rt<ad_ph(MU, 1)>(acc[a + 9], wh, sg);

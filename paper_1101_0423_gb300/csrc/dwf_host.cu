@@ -399,7 +399,7 @@ cudaError_t gauge_any(int prec, const double *U, void *G, Geom g, int par, int s
 }
 
 size_t link_bytes_per_site(int prec) {
-  return prec == P_F64 ? 8 * 18 * 8 : prec == P_F32 ? 8 * 18 * 4 : 8 * 12 * 2;
+  return prec == P_F64 ? 8 * 18 * 8 : prec == P_F32 ? 8 * 20 * 4 : 8 * 12 * 2;
 }
 
 // doubled gauge field of precision prec, built on first use
@@ -1463,7 +1463,9 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
     o.flops = n * (o.iters * flops_cg_iter(c->Ns) + o.restarts * flops_restart(c->Ns) +
                    (full ? flops_prep_recon(c->Ns) : 0.0));
     o.time_ms = ms;
-    o.bytes_hop_m5 = n * (2.0 * site_bytes(S.prec) + 8.0 * link_bytes_per_site(S.prec) / 8.0 / c->Ns);
+    // algorithmic bytes: 18 (16-bit: 12) reals per link, whatever padding the layout adds
+    const double lb = S.prec == P_F64 ? 144.0 : S.prec == P_F32 ? 72.0 : 24.0;
+    o.bytes_hop_m5 = n * (2.0 * site_bytes(S.prec) + 8.0 * lb / c->Ns);
     o.inner_prec_used = S.prec;
     o.escalations = escalations;
     o.kernel_launches = c->launches - launches0;
