@@ -38,8 +38,7 @@ PAPER_BEST_GFLOPS = 233.0  # GTX 480, CG (mixed), same lattice (Table 1): other 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch, bytes, of the
 # FP32 kernel classes at this workload, from profiles/k_hop_f32_16x16x16x32_Ns16.md.  It is
 # valid only for the kernel source it was captured on; clear it when k_hop changes.
-NCU_TRAFFIC = {"hop_m5": 146833920 + 69312768, "hop_xpay": 248027904 + 77827328,
-               "hop_update": 348585728 + 80604416, "smix_p": 302018560 + 242008064}
+NCU_TRAFFIC = {}
 
 
 def flops_ccdag(n, ns):

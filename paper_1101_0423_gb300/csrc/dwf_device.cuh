@@ -248,8 +248,9 @@ __device__ __forceinline__ void phase(R &re, R &im) {
 // ------------------------------------------------------------------ packed FP32 pairs
 //
 // Blackwell executes two FP32 operations per instruction on a 64-bit register pair
-// (add/sub/mul/fma .rn.f32x2).  A complex number (re, im) is such a pair, so a complex
-// multiply-accumulate w h + a costs two packed FMAs:  (wr, wr) h + (-wi, wi) (him, hre) + a.
+// (add/sub/mul/fma .rn.f32x2).  A complex number (re, im) is such a pair; a sum of
+// complex products sum_b w_b h_b is two packed FMA chains, P = sum_b w_b (hr_b, hr_b) and
+// Q = sum_b w_b (hi_b, hi_b), joined as P + (-1, 1) (Q.y, Q.x).
 
 struct f2 {
   unsigned long long v;
@@ -305,41 +306,9 @@ __device__ __forceinline__ f2 add_phase_rt(f2 up, f2 z, const SignPairs &sg) {
   else return fma2(swp2(z), sg.nsa, up);                          // -i z = (zi, -zr)
 }
 
-// acc += (1 + S g_mu) W psi with S = +-1 at run time (forward hops S = -1, backward S = +1),
-// so the two threads of a pair run the same instructions
-template <int MU>
-__device__ __forceinline__ void hop_dir_f2s(f2 (&acc)[12], const f2 (&ps)[12], const float4 *Wp,
-                                            const SignPairs &sg) {
-  f2 h[2][3], hs[2][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    h[0][a] = add_phase_rt<a_ph(MU, 0)>(ps[a], ps[a + 3 * (2 + a_col(MU, 0))], sg);
-    h[1][a] = add_phase_rt<a_ph(MU, 1)>(ps[a + 3], ps[a + 3 * (2 + a_col(MU, 1))], sg);
-    hs[0][a] = swp2(h[0][a]);
-    hs[1][a] = swp2(h[1][a]);
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float4 w0 = Wp[3 * a], w1 = Wp[3 * a + 1], w2 = Wp[3 * a + 2];
-    const f2 A0 = pk2(w0.x, w0.y), B0 = pk2(w0.z, w0.w);
-    const f2 A1 = pk2(w1.x, w1.y), B1 = pk2(w1.z, w1.w);
-    const f2 A2 = pk2(w2.x, w2.y), B2 = pk2(w2.z, w2.w);
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      f2 wh = mul2(A0, h[j][0]);
-      wh = fma2(B0, hs[j][0], wh);
-      wh = fma2(A1, h[j][1], wh);
-      wh = fma2(B1, hs[j][1], wh);
-      wh = fma2(A2, h[j][2], wh);
-      wh = fma2(B2, hs[j][2], wh);
-      acc[a + 3 * j] = add2(acc[a + 3 * j], wh);
-      if (ad_col(MU, 0) == j) acc[a + 6] = add_phase_rt<ad_ph(MU, 0)>(acc[a + 6], wh, sg);
-      if (ad_col(MU, 1) == j) acc[a + 9] = add_phase_rt<ad_ph(MU, 1)>(acc[a + 9], wh, sg);
-    }
-  }
-}
-
-// FP32 hop along MU with the link as stored (nine complex entries, 16-byte aligned pairs):
+// acc += (1 + S g_mu) W psi in FP32 pairs, with S = +-1 at run time (forward hops S = -1,
+// backward S = +1, so the eight directions run the same instructions) and the link as
+// stored (nine complex entries, pairs of them 16-byte aligned):
 // W h = P + (-1, 1) (Q.y, Q.x) with P = sum_b W_b (hr_b, hr_b), Q = sum_b W_b (hi_b, hi_b)
 template <int MU>
 __device__ __forceinline__ void hop_dir_raw(f2 (&acc)[12], const f2 (&ps)[12], const float4 *Wl,

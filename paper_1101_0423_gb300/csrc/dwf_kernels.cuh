@@ -230,8 +230,8 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(
 // dynamic shared memory of k_hop, in bytes:
 //   [mbarrier, 64 B][links as copied][neighbour indices][links packed for f32x2][stage][K]
 // FP32 and FP64 kernels use the links as copied (FP32 links are padded to 80 bytes, so the
-// nine complex entries are five aligned float4); the 16-bit forms expand each tile's links
-// into nine 16-byte entries (wr, wr, -wi, wi), rebuilding the third row.
+// nine complex entries are five aligned float4); the 16-bit forms rebuild each link's third
+// row and expand the tile's links into that same FP32 form.
 //
 // Layout: mbarriers; `nb` buffers of raw links and of neighbour indices (filled by TMA bulk
 // copies: two when a persistent CTA receives the next tile while computing this one); the
@@ -259,7 +259,7 @@ template <int P> struct HopSmem {
   // FP32 links are used as copied; the 16-bit forms are expanded
   static constexpr bool EXPAND = F2 && P != P_F32;
   __host__ __device__ static size_t off_k(int spb, int Ns, int nb, bool has_m) {
-    const size_t e = off_exp(spb, nb) + (EXPAND ? (size_t)spb * 8 * 9 * 16 : 0);
+    const size_t e = off_exp(spb, nb) + (EXPAND ? (size_t)spb * 8 * 5 * 16 : 0);
     const size_t st = has_m ? 64 + stage(spb, Ns) : 0;
     return align16(e > st ? e : st);
   }
@@ -402,12 +402,13 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
       }
     }
     if constexpr (SM::EXPAND) {
-      // expand every link once: nine (wr, wr, -wi, wi) entries; rebuild row 3 of 16-bit links
+      // 16-bit links: rebuild row 3 and expand each link into the padded FP32 form
       for (int l = tid; l < nsite * 8; l += nthr) {
         float W[18];
         load_link<P>(sL + (size_t)l * T::LREALS, W);
 #pragma unroll
-        for (int e = 0; e < 9; ++e) sP[(size_t)l * 9 + e] = make_float4(W[2 * e], W[2 * e], -W[2 * e + 1], W[2 * e + 1]);
+        for (int e = 0; e < 4; ++e) sP[(size_t)l * 5 + e] = make_float4(W[4 * e], W[4 * e + 1], W[4 * e + 2], W[4 * e + 3]);
+        sP[(size_t)l * 5 + 4] = make_float4(W[16], W[17], 0.f, 0.f);
       }
       __syncthreads();
     }
@@ -420,8 +421,8 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
 #pragma unroll
         for (int q = 0; q < 12; ++q) ac2[q] = pk2(0.f, 0.f);
         const SignPairs fw = sign_pairs(-1.f), bw = sign_pairs(1.f);
-        const float4 *myP = sP + (size_t)sl * 8 * 9;
-        const float4 *myW = reinterpret_cast<const float4 *>(sL) + (size_t)sl * 8 * 5;
+        const float4 *myW =
+            (SM::EXPAND ? sP : reinterpret_cast<const float4 *>(sL)) + (size_t)sl * 8 * 5;
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
           float ps1[24];
@@ -429,28 +430,15 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
           f2 ps[12];
 #pragma unroll
           for (int q = 0; q < 12; ++q) ps[q] = pk2(ps1[2 * q], ps1[2 * q + 1]);
-          if constexpr (SM::EXPAND) {
-            switch (d) {  // forward hops (1 - g_mu), then backward hops (1 + g_mu)
-              case 0: hop_dir_f2s<0>(ac2, ps, myP, fw); break;
-              case 1: hop_dir_f2s<1>(ac2, ps, myP + 9, fw); break;
-              case 2: hop_dir_f2s<2>(ac2, ps, myP + 18, fw); break;
-              case 3: hop_dir_f2s<3>(ac2, ps, myP + 27, fw); break;
-              case 4: hop_dir_f2s<0>(ac2, ps, myP + 36, bw); break;
-              case 5: hop_dir_f2s<1>(ac2, ps, myP + 45, bw); break;
-              case 6: hop_dir_f2s<2>(ac2, ps, myP + 54, bw); break;
-              default: hop_dir_f2s<3>(ac2, ps, myP + 63, bw); break;
-            }
-          } else {
-            switch (d) {
-              case 0: hop_dir_raw<0>(ac2, ps, myW, fw); break;
-              case 1: hop_dir_raw<1>(ac2, ps, myW + 5, fw); break;
-              case 2: hop_dir_raw<2>(ac2, ps, myW + 10, fw); break;
-              case 3: hop_dir_raw<3>(ac2, ps, myW + 15, fw); break;
-              case 4: hop_dir_raw<0>(ac2, ps, myW + 20, bw); break;
-              case 5: hop_dir_raw<1>(ac2, ps, myW + 25, bw); break;
-              case 6: hop_dir_raw<2>(ac2, ps, myW + 30, bw); break;
-              default: hop_dir_raw<3>(ac2, ps, myW + 35, bw); break;
-            }
+          switch (d) {  // forward hops (1 - g_mu), then backward hops (1 + g_mu)
+            case 0: hop_dir_raw<0>(ac2, ps, myW, fw); break;
+            case 1: hop_dir_raw<1>(ac2, ps, myW + 5, fw); break;
+            case 2: hop_dir_raw<2>(ac2, ps, myW + 10, fw); break;
+            case 3: hop_dir_raw<3>(ac2, ps, myW + 15, fw); break;
+            case 4: hop_dir_raw<0>(ac2, ps, myW + 20, bw); break;
+            case 5: hop_dir_raw<1>(ac2, ps, myW + 25, bw); break;
+            case 6: hop_dir_raw<2>(ac2, ps, myW + 30, bw); break;
+            default: hop_dir_raw<3>(ac2, ps, myW + 35, bw); break;
           }
         }
 #pragma unroll
