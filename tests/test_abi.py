@@ -77,3 +77,25 @@ def test_create_rejects_invalid_arguments_before_touching_cuda(lib, dims, ns, m0
     with pytest.raises(dwf.DwfError) as e:
         dwf.dwf_create(dims, ns, m0, 0.05, om, np.zeros(n))
     assert e.value.status == dwf.DWF_EINVAL
+
+
+@pytest.mark.parametrize("ns", [1, 2, 5, 8, 16, 24, 64])
+@pytest.mark.parametrize("kind", ["shamir", "borici", "cosine", "random"])
+@pytest.mark.parametrize("mq", [0.0, 0.02, 0.7])
+def test_create_builds_the_m5_recurrence_for_any_valid_weights(lib, ns, kind, mq):
+    """dwf_create derives M5 and M5^T of Eq. 8 twice -- dense, from the cyclic bidiagonal
+    structure, and as the recurrence tables of the FP64 hop epilogue -- and refuses the
+    context (DWF_EINVAL) if the two disagree anywhere; this happens before any CUDA call.
+    So a valid configuration may only fail later, at CUDA (no GPU here), never with EINVAL."""
+    from paper_1101_0423_gb300 import dwf, inputs
+    if kind == "random":
+        rng = np.random.default_rng(ns)
+        om, sg = rng.uniform(0.3, 1.7, ns), rng.uniform(-0.5, 1.2, ns)
+    else:
+        om, sg = inputs.weights(kind, ns)
+    try:
+        h = dwf.dwf_create((4, 4, 4, 4), ns, 1.8, mq, om, sg)
+    except dwf.DwfError as e:
+        assert e.status != dwf.DWF_EINVAL, "recurrence tables disagree with the dense M5"
+    else:
+        dwf.dwf_destroy(h)
