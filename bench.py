@@ -305,6 +305,35 @@ def serve_measure(n, lattices, inner_prec, fractions):
     return out
 
 
+def odwf_measure(repeats=3):
+    """The optimal domain-wall operator: sigma = omega = the optimal weights for |H_w| in
+    [0.05, 6.2] (dwf_optimal_weights), on the 16^3 x 32 x 16 lattice, source, gauge and
+    mass of the default line, against the cosine weights of that line.  FP32 inner, 1e-10."""
+    import torch
+    from paper_1101_0423_gb300 import dwf, inputs
+    lmin, lmax = 0.05, 6.2
+    om_opt, delta = dwf.dwf_optimal_weights(NS, lmin, lmax)
+    U = inputs.gauge_field(DIMS, EPS, seed=SEED)
+    eta = inputs.gaussian_source(DIMS, NS, seed=SEED)
+    stream = torch.cuda.current_stream()
+    rows = {}
+    for name, (om, sg) in {"optimal": (om_opt, om_opt), "cosine": inputs.weights("cosine", NS)}.items():
+        with dwf.Context(DIMS, NS, M0, MQ, om, sg, U) as ctx:
+            d_eta = torch.from_numpy(eta).cuda()
+            d_psi = torch.empty_like(d_eta)
+            dwf.dwf_solve_dev(ctx.h, d_eta, d_psi, stream=stream)  # warm-up
+            times, st = [], None
+            for _ in range(repeats):
+                st = dwf.dwf_solve_dev(ctx.h, d_eta, d_psi, stream=stream)
+                times.append(st["time_ms"])
+            ms = statistics.median(times)
+            rows[name] = {"solve_ms": ms, "gflops": st["flops"] / (ms * 1e-3) / 1e9, "iters": st["iters"],
+                          "restarts": st["restarts"], "true_res_full": st["true_res_full"]}
+    return {"workload": "optimal domain-wall weights (sigma = omega, |H_w| in [0.05, 6.2]), 16^3x32xNs16, "
+                        "mq 0.02, fp32 inner, tol 1e-10", "delta": delta, "omega": [float(w) for w in om_opt],
+            **rows}
+
+
 def batch_measure():
     """12 spin-colour point sources on 24^3 x 48 x 16 Shamir (mq = 0.01): one batched solve
     against the same 12 solved one after another; and a ragged set of 8 right-hand sides on
@@ -393,6 +422,8 @@ def main():
                     help="only the batched workloads: 12 point sources on 24^3x48x16, ragged 8-rhs set")
     ap.add_argument("--serve", action="store_true",
                     help="only the served sweep: 40 requests over all four lattices at 0.2..0.95 of capacity")
+    ap.add_argument("--odwf", action="store_true",
+                    help="only the optimal-weights solve on 16^3x32x16 against the cosine weights")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -401,6 +432,11 @@ def main():
         _b.build()
         for row in batch_measure():
             print(json.dumps(row))
+        return
+    if args.odwf:
+        from paper_1101_0423_gb300 import build as _b
+        _b.build()
+        print(json.dumps(odwf_measure()))
         return
     if args.serve:
         from paper_1101_0423_gb300 import build as _b, dwf

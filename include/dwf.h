@@ -298,6 +298,20 @@ dwf_status dwf_poll(dwf_server *srv, uint64_t ticket, double *psi_out, dwf_resul
 /* Latency percentiles, throughput and occupancy of the server so far. */
 dwf_status dwf_server_get_stats(dwf_server *srv, dwf_server_stats *stats);
 
+/* Weights of the optimal domain-wall operator (sigma = omega in Eq. 1; Sec. 2.1 takes them
+ * "such that the maximal chiral symmetry is attained" from a formula it only cites).
+ * Reading: the omega_s that make S(lam) = (1 - T)/(1 + T), T = prod_s (1 - omega_s lam) /
+ * (1 + omega_s lam), the best uniform approximation of sgn(lam) on [lambda_min, lambda_max],
+ * the range of |H_w| = |g5 D_w| the caller supplies; computed by the Remez exchange (the
+ * error 1 - S alternates Ns + 1 times).  Host computation only: needs no context or GPU.
+ * omega receives Ns weights, caller-owned, in decreasing order (the four-dimensional
+ * operator does not depend on their order along s); delta, if not NULL, receives
+ * max |1 - S| on the interval.  DWF_EINVAL: Ns outside 1..64, lambda_min <= 0,
+ * lambda_max <= lambda_min, or omega NULL.  DWF_ENOCONV: the exchange did not settle (seen
+ * only where delta would fall tens of orders below double precision, e.g. Ns = 64 on a
+ * spectrum narrower than a factor of 2). */
+dwf_status dwf_optimal_weights(int Ns, double lambda_min, double lambda_max, double *omega, double *delta);
+
 /* Text of the last error on ctx ("" if none); valid until the next call on ctx. */
 const char *dwf_last_error(const dwf_ctx *ctx);
 /* Name of a status code. */

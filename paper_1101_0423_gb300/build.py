@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdwf_gb300.so")
-SOURCES = ["k_f64.cu", "k_f32.cu", "k_half.cu", "dwf_host.cu", "dwf_server.cu"]
+SOURCES = ["k_f64.cu", "k_f32.cu", "k_half.cu", "dwf_host.cu", "dwf_server.cu", "dwf_weights.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

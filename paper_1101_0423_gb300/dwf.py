@@ -126,6 +126,7 @@ def load(build_if_missing: bool = True):
         "dwf_submit": ([vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], i),
         "dwf_poll": ([vp, ctypes.c_uint64, dp, ctypes.POINTER(Result)], i),
         "dwf_server_get_stats": ([vp, ctypes.POINTER(ServerStats)], i),
+        "dwf_optimal_weights": ([i, d, d, dp, dp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -171,6 +172,17 @@ def dwf_solve_params_default() -> SolveParams:
     p = SolveParams()
     load().dwf_solve_params_default(ctypes.byref(p))
     return p
+
+
+def dwf_optimal_weights(Ns, lambda_min, lambda_max):
+    """(omega, delta): the optimal domain-wall weights for |H_w| in [lambda_min, lambda_max]
+    (decreasing) and the deviation max |1 - S| of their sign-function approximation."""
+    omega = np.zeros(max(int(Ns), 1))
+    delta = ctypes.c_double(0.0)
+    st = load().dwf_optimal_weights(int(Ns), float(lambda_min), float(lambda_max), _dp(omega), ctypes.byref(delta))
+    if st != DWF_OK:
+        raise DwfError(st, "dwf_optimal_weights: invalid range or no convergence")
+    return omega[:int(Ns)], delta.value
 
 
 def dwf_create(dims, Ns, m0, mq, omega, sigma):

@@ -128,3 +128,22 @@ def test_bf16_inner_escalates_to_fp32_when_defect_correction_stalls(gpu_lib):
         psi, st = dwf.dwf_solve(ctx.h, eta, inner_prec=dwf.PREC_BF16, tol=1e-10)
     assert st["converged"] == 1 and st["true_res_full"] <= 1e-10
     assert st["escalations"] == 1 and st["inner_prec_used"] == dwf.PREC_F32
+
+
+@pytest.mark.parametrize("ns", [8, 12])
+def test_full_solve_with_optimal_weights(gpu_lib, ns):
+    """The optimal domain-wall operator (sigma = omega = the optimal weights for |H_w| in
+    [0.05, 6.2], computed by the oracle) solved through the C-ABI; the oracle recomputes
+    |eta - D psi| / |eta| and solves the same system."""
+    from oracle import weights as OW
+    from paper_1101_0423_gb300 import dwf
+    dims, mq = (4, 4, 4, 6), 0.02
+    om, _ = OW.optimal_weights(ns, 0.05, 6.2)
+    U = inputs.gauge_field(dims, 0.5, seed=14)
+    eta = inputs.gaussian_source(dims, ns, seed=15)
+    with dwf.Context(dims, ns, M0, mq, om, om, U) as ctx:
+        psi, st = dwf.dwf_solve(ctx.h, eta, tol=1e-10)
+    res = np.linalg.norm(eta - oracle.dfull(dims, ns, U, M0, mq, om, om, psi)) / np.linalg.norm(eta)
+    assert res <= 1e-10 and st["converged"] == 1
+    psi_or, _, _ = oracle.solve_full(dims, ns, U, M0, mq, om, om, eta, tol=1e-13)
+    assert relnorm(psi, psi_or) < 1e-6
