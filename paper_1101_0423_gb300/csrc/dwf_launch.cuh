@@ -18,7 +18,7 @@ inline int sites_per_block(int P, int Ns) {
 }
 
 // sites per CTA of k_hop, whose CTA is (Ns, spb): 128 threads measured best at Ns = 16
-// (94 us against 103 us with 256 and 139 us with 512 for the FP32 hop + M5)
+// (against 256 and 512 threads, and 64 and 96, for the FP32 hop kernels)
 inline int hop_sites_per_block(int P, int Ns) {
   const int target = 128;
   (void)P;
