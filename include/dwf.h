@@ -177,8 +177,9 @@ dwf_status dwf_apply_eo_dev(dwf_ctx *ctx, int op, int prec, int parity, const do
  * dwf_solve layout one after another; stats, if not NULL, receives nrhs entries.  Every
  * right-hand side has its own CG scalars, restarts and convergence (Algorithm 1-2, Sec. 2.3);
  * all of them advance in the same kernel launches (one grid row per right-hand side) and the
- * same CUDA graph.  A full-system batch aims its Schur residual at tol/4 (no second pass);
- * the 16-bit-to-FP32 escalation of AUTO mode applies to single solves only.  Returns the
+ * same CUDA graph.  As for a single full-system solve, a right-hand side whose full residual
+ * misses tol continues once with a tighter Schur target; the 16-bit-to-FP32 escalation of
+ * AUTO mode applies to single solves only.  Returns the
  * first failure among the right-hand sides (DWF_ENOCONV if any did not converge). */
 dwf_status dwf_solve_batch(dwf_ctx *ctx, int nrhs, const double *rhs, double *sol,
                            const dwf_solve_params *params, dwf_solve_stats *stats);

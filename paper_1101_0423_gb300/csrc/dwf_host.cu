@@ -1180,7 +1180,7 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
   // the full-system residual runs a little above the Schur one (by at most cond(S1)): the
   // Schur system of a full solve aims at half the tolerance (a quarter in batches, which
   // have no second pass)
-  const double tol_schur = full ? (K == 1 ? 0.5 : 0.25) * prm.tol : prm.tol;
+  const double tol_schur = full ? 0.5 * prm.tol : prm.tol;
   std::vector<RhsState> R(K);
   int escalations = 0;
 
@@ -1422,15 +1422,24 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
   if (loop_st != DWF_OK && loop_st != DWF_ENOCONV) return loop_st;
   if (full) {
     for (int k = 0; k < K; ++k) TRY(reconstruct(k));
-    // single system: if the full residual still misses the target, tighten the Schur
-    // tolerance once and continue from x_hat
-    if (K == 1 && R[0].converged && R[0].res_full > prm.tol) {
-      const double tighter = tol_schur * std::min(0.1, 0.5 * prm.tol / R[0].res_full);
-      R[0].done = R[0].converged = false;
-      TRY(arm(0, tighter, false, R[0].mode == DWF_MODE_DEFECT, R[0].rr_last));
+    // a system whose full residual still misses the target continues from x_hat with the
+    // Schur tolerance tightened once (one common target for those of a batch; the others
+    // stay parked)
+    double tighter = tol_schur;
+    std::vector<int> again;
+    for (int k = 0; k < K; ++k)
+      if (R[k].converged && R[k].res_full > prm.tol) {
+        again.push_back(k);
+        tighter = std::min(tighter, tol_schur * std::min(0.1, 0.5 * prm.tol / R[k].res_full));
+      }
+    if (!again.empty()) {
+      for (int k : again) {
+        R[k].done = R[k].converged = false;
+        TRY(arm(k, tighter, false, R[k].mode == DWF_MODE_DEFECT, R[k].rr_last));
+      }
       loop_st = cg_loop(tighter);
       if (loop_st != DWF_OK && loop_st != DWF_ENOCONV) return loop_st;
-      TRY(reconstruct(0));
+      for (int k : again) TRY(reconstruct(k));
     }
   } else {
     CK(cudaMemsetAsync(d_sol, 0, (size_t)K * full_doubles * sizeof(double), st));

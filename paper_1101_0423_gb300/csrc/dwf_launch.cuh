@@ -49,8 +49,9 @@ cudaError_t hop_go(const HopArgs &a, cudaStream_t st) {
   const long ntile = (a.h + spb - 1) / spb;
   long nblk = ntile;  // one tile per CTA
   if constexpr (hop_persistent<EPI>()) {
-    // persistent grid: as many CTAs as are resident at once (shared among the right-hand
-    // sides of a batch), each taking an equal number of tiles
+    // persistent grid: as many CTAs per right-hand side as are resident at once, each taking
+    // an equal number of tiles (the rows of a batch follow one another through the GPU, and
+    // a finished right-hand side's row returns at once)
     const int nthr = a.Ns * spb;
     const unsigned long long key = ((unsigned long long)smem << 20) | (unsigned long long)nthr;
     static std::atomic<unsigned long long> cached_key{0};
@@ -66,8 +67,7 @@ cudaError_t hop_go(const HopArgs &a, cudaStream_t st) {
       cached_res.store(res);
       cached_key.store(key);
     }
-    const long slots = std::max(1L, res / nrhs);
-    const long per_cta = (ntile + slots - 1) / slots;
+    const long per_cta = (ntile + res - 1) / res;
     nblk = (ntile + per_cta - 1) / per_cta;
   }
   k_hop<P, EPI, NSC><<<dim3((unsigned)nblk, nrhs), dim3(a.Ns, spb), smem, st>>>(a);
