@@ -288,16 +288,23 @@ def serve_run(reqs, lam, gauges_np, inner_prec, max_inflight=4, budget_gb=150.0,
         dwf.dwf_server_destroy(srv)
 
 
-def serve_measure(n, lattices, inner_prec, fractions):
-    """Capacity from the requests solved one after another, then Poisson runs at each fraction."""
+def serve_measure(n, lattices, inner_prec, fractions, progress=False):
+    """Capacity from the requests solved one after another, then Poisson runs at each
+    fraction.  A run at fraction f lasts about n / (f x capacity) seconds."""
     from paper_1101_0423_gb300 import inputs
     reqs = serve_requests(n, lattices)
     gauges_np = {d: inputs.gauge_field(d, EPS, seed=10 + i) for i, d in enumerate(SERVE_LATTICES_FULL)
                  if d in {r["dims"] for r in reqs}}
     seq = serve_run(reqs, 1e9, gauges_np, inner_prec, max_inflight=1)   # back to back, one at a time
     capacity = seq["solves_per_s"]
+    if progress:
+        est = sum(n / (f * capacity) for f in fractions)
+        print(f"serve: capacity {capacity:.3f} solves/s; the {len(fractions)} arrival-rate runs take about "
+              f"{est / 60:.0f} min", file=sys.stderr, flush=True)
     out = []
     for f in fractions:
+        if progress:
+            print(f"serve: lambda = {f} x capacity ({n} requests)", file=sys.stderr, flush=True)
         st = serve_run(reqs, f * capacity, gauges_np, inner_prec)
         out.append({"lambda_fraction": f, "lambda_per_s": f * capacity, "capacity_per_s": capacity,
                     "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
@@ -422,6 +429,8 @@ def main():
                     help="only the batched workloads: 12 point sources on 24^3x48x16, ragged 8-rhs set")
     ap.add_argument("--serve", action="store_true",
                     help="only the served sweep: 40 requests over all four lattices at 0.2..0.95 of capacity")
+    ap.add_argument("--serve-requests", type=int, default=40,
+                    help="requests per arrival-rate run of --serve (the sweep lasts about 12.5 x this / capacity)")
     ap.add_argument("--odwf", action="store_true",
                     help="only the optimal-weights solve on 16^3x32x16 against the cosine weights")
     args = ap.parse_args()
@@ -441,7 +450,8 @@ def main():
     if args.serve:
         from paper_1101_0423_gb300 import build as _b, dwf
         _b.build()
-        for row in serve_measure(40, SERVE_LATTICES_FULL, dwf.PREC_BF16, [0.2, 0.4, 0.6, 0.8, 0.95]):
+        for row in serve_measure(args.serve_requests, SERVE_LATTICES_FULL, dwf.PREC_BF16,
+                                 [0.2, 0.4, 0.6, 0.8, 0.95], progress=True):
             print(json.dumps({"metric": "served solves/s, p99 latency", "config": {
                 "workload": "served: uniform lattice {8^4,12^3x24,16^3x32,24^3x48} x Ns {8,16,24,32} x "
                             "mq U[0.005,0.1] x {shamir,borici,cosine}, bf16 inner, tol 1e-10, 150 GB budget"},
