@@ -228,17 +228,15 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
 // dynamic shared memory of k_hop, in bytes:
-//   [mbarrier, 64 B][links as copied][neighbour indices][links packed for f32x2][stage][K]
-// FP32 and FP64 kernels use the links as copied (FP32 links are padded to 80 bytes, so the
-// nine complex entries are five aligned float4); the 16-bit forms rebuild each link's third
-// row and expand the tile's links into that same FP32 form.
-//
-// Layout: mbarriers; `nb` buffers of raw links and of neighbour indices (filled by TMA bulk
-// copies: two when a persistent CTA receives the next tile while computing this one); the
-// tile's expanded links; M5.  The M5 staging rows overlay the link buffers from the start
-// (kernels with an M5 epilogue take one tile per CTA, so all of them are dead by then).
-// Shared memory is kept small on purpose: what the CTAs leave of the SM's 256 KB is the L1
-// that holds the neighbour gathers in flight.
+//   [mbarriers, 64][links as copied] x nb [neighbour indices] x nb [16-bit links expanded][M]
+// with nb = 2 when a persistent CTA receives the next tile while computing this one, else 1
+// (links and indices arrive by TMA bulk copies).  FP32 and FP64 kernels use the links as
+// copied (FP32 links are padded to 80 bytes, so the nine complex entries are five aligned
+// float4); the 16-bit forms rebuild each link's third row and expand the tile's links into
+// that same FP32 form.  The M5 staging rows overlay everything from offset 64 on (kernels
+// with an M5 epilogue take one tile per CTA, so the link buffers are dead by then).  Shared
+// memory is kept small on purpose: what the CTAs leave of the SM's 256 KB is the L1 that
+// holds the neighbour gathers in flight.
 template <int P> struct HopSmem {
   static constexpr bool F2 = !(P == P_F64);
   using RL = typename PT<P>::real;
@@ -279,9 +277,10 @@ __host__ __device__ inline size_t hop_smem_bytes(int spb, int Ns) {
   return HopSmem<P>::bytes(spb, Ns, hop_persistent<EPI>() ? 2 : 1, EpiT<EPI>::has_m);
 }
 
-// k_hop: one thread per (site, s), CTA = (Ns, spb) = one tile of spb sites; a grid of as
-// many CTAs as fit on the GPU at once walks all tiles.  Per tile: eight gathers of the
-// neighbours' spinors (Eq. 12), the hop sum in packed FP32 pairs (or FP64), the epilogue.
+// k_hop: one thread per (site, s), CTA = (Ns, spb) = one tile of spb sites (kernels without
+// an M5 epilogue: a grid of as many CTAs as fit on the GPU at once, walking all tiles).  Per
+// tile: eight gathers of the neighbours' spinors (Eq. 12), the hop sum in packed FP32 pairs
+// (or FP64), the epilogue.
 template <int P, int EPI, int NSC>
 __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
   // one right-hand side of a batch per grid row; fields are offset where they are used, so
