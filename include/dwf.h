@@ -110,7 +110,10 @@ typedef struct {
     int profile;       /* record CUDA events around every kernel class (default 0) */
     int stall_iters;   /* restart, resetting the search direction, when |r| has not reached a
                           new minimum for this many inner iterations; <= 0 selects 500 */
-    int reserved[5];
+    int schur_target_pct; /* full system: the Schur residual aims at this percentage of tol
+                          (<= 0 selects 50); a system whose full residual |eta - D psi| / |eta|
+                          still misses tol continues once with a tightened target */
+    int reserved[4];
 } dwf_solve_params;
 
 /* kernel classes timed when params.profile != 0 */

@@ -636,6 +636,7 @@ void dwf_solve_params_default(dwf_solve_params *p) {
   p->check_every = 8;
   p->use_graph = 1;
   p->profile = 0;
+  p->schur_target_pct = 50;
 }
 
 dwf_status dwf_create(const int dims[4], int Ns, double m0, double mq, const double *omega,
@@ -1178,9 +1179,9 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
   const size_t full_doubles = (size_t)c->V4 * c->Ns * 24;
   const size_t nbytes64 = field_bytes(c, P_F64);
   // the full-system residual runs a little above the Schur one (by at most cond(S1)): the
-  // Schur system of a full solve aims at half the tolerance (a quarter in batches, which
-  // have no second pass)
-  const double tol_schur = full ? 0.5 * prm.tol : prm.tol;
+  // Schur system of a full solve aims at schur_target_pct of the tolerance (default 50 %),
+  // and the systems that still miss it take one tightened pass below
+  const double tol_schur = full ? 0.01 * (prm.schur_target_pct > 0 ? prm.schur_target_pct : 50) * prm.tol : prm.tol;
   std::vector<RhsState> R(K);
   int escalations = 0;
 
@@ -1496,6 +1497,7 @@ dwf_status check_solve_args(dwf_ctx *c, dwf_solve_params *prm, const dwf_solve_p
   if (prm->mode < DWF_MODE_AUTO || prm->mode > DWF_MODE_DEFECT) return fail(c, DWF_EINVAL, "unknown mode");
   if (!(prm->tol > 0.0) || prm->max_iter < 1) return fail(c, DWF_EINVAL, "tol must be > 0 and max_iter >= 1");
   if (prm->check_every < 1) prm->check_every = 8;
+  if (prm->schur_target_pct > 100000) return fail(c, DWF_EINVAL, "schur_target_pct above 100000");
   return DWF_OK;
 }
 

@@ -39,7 +39,7 @@ class SolveParams(ctypes.Structure):
                 ("inner_prec", ctypes.c_int), ("mode", ctypes.c_int), ("system", ctypes.c_int),
                 ("schur_parity", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("profile", ctypes.c_int), ("stall_iters", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("schur_target_pct", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class SolveStats(ctypes.Structure):

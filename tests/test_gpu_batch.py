@@ -37,6 +37,22 @@ def test_full_system_batch_of_gaussian_sources(gpu_lib, prec):
         assert relnorm(sol[k], psi_or) < 1e-6
 
 
+def test_batch_takes_one_common_tightened_pass(gpu_lib):
+    """schur_target_pct = 10000 stops every right-hand side of the batch at a full residual
+    far above tol; those systems continue together with one common tightened target and
+    each ends at |eta - D psi| / |eta| <= 1e-10 (oracle)."""
+    dwf = gpu_lib
+    dims, ns, mq = (4, 4, 4, 4), 8, 0.03
+    om, sg = inputs.weights("cosine", ns)
+    U = inputs.gauge_field(dims, 0.5, seed=22)
+    rhs = np.stack([inputs.gaussian_source(dims, ns, seed=50 + k) for k in range(3)])
+    with dwf.Context(dims, ns, M0, mq, om, sg, U) as ctx:
+        sol, stats = dwf.dwf_solve_batch(ctx.h, rhs, schur_target_pct=10000)
+    for k in range(3):
+        assert stats[k]["converged"] == 1 and stats[k]["true_res_full"] <= 1e-10
+        assert relnorm(oracle.dfull(dims, ns, U, M0, mq, om, sg, sol[k]), rhs[k]) <= 1e-10
+
+
 def test_normal_system_batch_with_a_zero_source(gpu_lib):
     """4^4 x 8 Shamir normal equations on even sites; the third source is zero (finished from
     the start, must stay zero while the others iterate)."""

@@ -147,3 +147,21 @@ def test_full_solve_with_optimal_weights(gpu_lib, ns):
     assert res <= 1e-10 and st["converged"] == 1
     psi_or, _, _ = oracle.solve_full(dims, ns, U, M0, mq, om, om, eta, tol=1e-13)
     assert relnorm(psi, psi_or) < 1e-6
+
+
+def test_loose_schur_target_takes_the_tightened_pass(gpu_lib):
+    """A Schur target of 100 x tol (schur_target_pct = 10000) leaves the full residual of the
+    first pass far above tol; the solve must continue from its own x with a tightened target
+    and still end at |eta - D psi| / |eta| <= 1e-10 (oracle), with more iterations than a
+    solve whose first pass already meets it."""
+    from paper_1101_0423_gb300 import dwf
+    dims, ns, mq = (4, 4, 4, 6), 8, 0.02
+    om, sg = inputs.weights("cosine", ns)
+    U = inputs.gauge_field(dims, 0.5, seed=16)
+    eta = inputs.gaussian_source(dims, ns, seed=17)
+    with dwf.Context(dims, ns, M0, mq, om, sg, U) as ctx:
+        psi, st = dwf.dwf_solve(ctx.h, eta, tol=1e-10, schur_target_pct=10000)
+        _, st_loose = dwf.dwf_solve(ctx.h, eta, tol=1e-8, schur_target_pct=100)
+    res = np.linalg.norm(eta - oracle.dfull(dims, ns, U, M0, mq, om, sg, psi)) / np.linalg.norm(eta)
+    assert res <= 1e-10 and st["converged"] == 1 and st["true_res_full"] <= 1e-10
+    assert st["iters"] > st_loose["iters"]
