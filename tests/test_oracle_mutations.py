@@ -49,6 +49,14 @@ MUTATIONS = [
     ("S2 uses omega instead of sqrt(omega)", "S2[i * Ns + j] = Yi[i * Ns + j] * sqrt(omega[j]);",
      "S2[i * Ns + j] = Yi[i * Ns + j] * omega[j];",
      [lambda: pins.test_schur_solve_matches_dense_lu((2, 2, 2, 4), 3, "cosine", 1)]),
+    ("CG beta inverted", "double beta = rr_new / rr;", "double beta = rr / rr_new;",
+     [lambda: pins.test_cg_iterates_are_the_krylov_galerkin_solutions(7)]),
+    ("CG x stepped along the next direction",
+     "for (size_t i = 0; i < n; ++i) x[i] += alpha * pv[i];\n        for (size_t i = 0; i < n; ++i) pv[i] = r[i] + beta * pv[i];",
+     "for (size_t i = 0; i < n; ++i) pv[i] = r[i] + beta * pv[i];\n        for (size_t i = 0; i < n; ++i) x[i] += alpha * pv[i];",
+     [lambda: pins.test_cg_iterates_are_the_krylov_galerkin_solutions(7)]),
+    ("L+ and L- swapped in D", "spin < 2 ? Mp : Mm", "spin < 2 ? Mm : Mp",
+     [lambda: pins.test_free_5d_operator_momentum_block((4, 6, 2, 8), 4)]),
 ]
 
 

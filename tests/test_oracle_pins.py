@@ -64,6 +64,42 @@ def test_free_field_momentum_closed_form(dims):
         assert rel(out, want) < 1e-13
 
 
+def eq4_l(ns, mq):
+    """L+ and L- of Eq. 3-4 (0-based s): (L+)_{s,s-1} = 1, corner (L+)_{0,Ns-1} = -mq/(2 m0)."""
+    Lp = np.zeros((ns, ns))
+    for s in range(1, ns):
+        Lp[s, s - 1] = 1.0
+    Lp[0, ns - 1] = -mq / (2 * M0)
+    return Lp, Lp.T
+
+
+@pytest.mark.parametrize("dims,ns", [((4, 6, 2, 8), 4), ((2, 4, 6, 4), 3)])
+def test_free_5d_operator_momentum_block(dims, ns):
+    """U = 1: D of Eq. 1 maps e^{ipx} chi to e^{ipx} D(p) chi with the 4Ns x 4Ns (per colour)
+    block D(p) chi = D_w(p) [(omega + sigma L) chi] + (1 - L) chi, where D_w(p) is the free
+    Wilson matrix of the momentum and L = P+ L+ + P- L- acts along s (Eq. 3-4).  Distinct
+    random omega and sigma, so no weight can stand in for the other."""
+    mq = 0.07
+    U = inputs.unit_gauge(dims)
+    g = dense.gammas()[0]
+    coords = np.array(dense.coords(dims))
+    rng = np.random.default_rng(17)
+    om, sg = rng.uniform(0.5, 1.5, ns), rng.uniform(-0.4, 0.9, ns)
+    Lp, Lm = eq4_l(ns, mq)
+    for n in [(0, 0, 0, 0), (1, 0, 0, 0), (0, 2, 0, 1), (1, 1, 1, 3)]:
+        p = 2 * np.pi * np.array(n) / np.array(dims)
+        chi = rng.normal(size=(ns, 4, 3)) + 1j * rng.normal(size=(ns, 4, 3))
+        phase = np.exp(1j * coords @ p)
+        psi = phase[:, None, None, None] * chi[None]
+        out = cview(oracle.dfull(dims, ns, U, M0, mq, om, sg, psi.view(np.float64).reshape(-1)), dims, ns)
+        Lchi = np.concatenate([np.einsum("st,tac->sac", Lp, chi[:, :2]), np.einsum("st,tac->sac", Lm, chi[:, 2:])],
+                              axis=1)
+        chi1 = om[:, None, None] * chi + sg[:, None, None] * Lchi
+        Dp = (4 - M0 - np.cos(p).sum()) * np.eye(4) + 1j * sum(g[mu] * np.sin(p[mu]) for mu in range(4))
+        block = np.einsum("ab,sbc->sac", Dp, chi1) + chi - Lchi
+        assert rel(out, phase[:, None, None, None] * block[None]) < 1e-13
+
+
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 4, 6, 4)])
 def test_gamma5_hermiticity_of_dw(dims):
     """<chi, g5 D_w g5 psi> = <D_w chi, psi> for a random gauge field."""
@@ -362,3 +398,35 @@ def test_cg_reaches_tolerance_config0_size():
     # residual recomputed outside the CG routine
     r = b - oracle.ccdag_op(dims, ns, U, mp, mm, 0, x)
     assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-12
+
+
+@pytest.mark.parametrize("k", [3, 7])
+def test_cg_iterates_are_the_krylov_galerkin_solutions(k):
+    """Algorithm 1 from x0 = 0 stopped after k iterations gives the x in the Krylov space
+    K_k = span{b, Ab, ..., A^{k-1} b} whose residual is orthogonal to K_k (A = C C^dag
+    Hermitian positive definite): the defining property of CG, which holds only if every
+    alpha and beta is right and the search directions are A-conjugate.  The Galerkin solution
+    is formed here from an orthonormal basis of K_k and a k x k solve."""
+    dims, ns, mq, p = (4, 4, 4, 4), 4, 0.05, 1
+    U = inputs.gauge_field(dims, 0.5, seed=121)
+    om, sg = inputs.weights("cosine", ns)
+    mp, mm = oracle.m5(ns, M0, mq, om, sg)
+    b = inputs.gaussian_source(dims, ns, seed=122, parity=p)
+    A = lambda v: oracle.ccdag_op(dims, ns, U, mp, mm, p, np.ascontiguousarray(v).view(np.float64)).view(np.complex128)
+    bc = b.view(np.complex128)
+    Q = np.zeros((bc.size, k), complex)
+    v = bc.copy()
+    for j in range(k):  # Arnoldi with Gram-Schmidt applied twice
+        for _ in range(2):
+            v = v - Q[:, :j] @ (Q[:, :j].conj().T @ v)
+        Q[:, j] = v / np.linalg.norm(v)
+        v = A(Q[:, j])
+    AQ = np.stack([A(Q[:, j]) for j in range(k)], axis=1)
+    y = np.linalg.solve(Q.conj().T @ AQ, Q.conj().T @ bc)
+    x_gal = Q @ y
+    x, iters, _ = oracle.cg(dims, ns, U, mp, mm, p, b, tol=1e-300, maxiter=k)
+    assert iters == k
+    xc = x.view(np.complex128)
+    assert np.linalg.norm(xc - x_gal) / np.linalg.norm(x_gal) < 1e-10
+    r = bc - A(xc)
+    assert np.linalg.norm(Q.conj().T @ r) < 1e-10 * np.linalg.norm(r)
