@@ -5,7 +5,8 @@ Tolerance (max |gpu - oracle| / max |oracle|): FP64 1e-12 and FP32 1e-5 (the req
 bars), fp16 5e-3 and bf16 3e-2 (per-(site,s) normalised 16-bit storage: unit roundoff
 2^-11 resp. 2^-8 of the site's largest component, a few roundings per operator).
 Lattices span several CTA tiles and a ragged last tile (Ns = 5, 12 and 6^4 x 16 do not
-divide the sites-per-CTA count), asymmetric extents catch transposed directions.
+divide the sites-per-CTA count), asymmetric extents catch transposed directions; Ns = 32
+with mq = 0 and Ns = 64 (the largest accepted) cover the edges of the fifth dimension.
 """
 import numpy as np
 import pytest
@@ -23,6 +24,8 @@ LATTICES = [
     ((2, 4, 6, 4), 5, "cosine", 0.02),
     ((6, 4, 2, 8), 12, "borici", 0.1),
     ((6, 6, 6, 6), 16, "cosine", 0.02),
+    ((2, 2, 4, 4), 32, "shamir", 0.0),   # mq = 0: L+ without its corner
+    ((2, 2, 2, 4), 64, "cosine", 0.02),  # the largest Ns the library accepts
 ]
 
 

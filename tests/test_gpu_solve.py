@@ -83,7 +83,7 @@ def test_zero_source(config0):
 
 FULL_CASES = [((4, 4, 4, 4), 8, "cosine", 0.05, 1), ((4, 4, 4, 4), 8, "borici", 0.02, 0),
               ((2, 4, 6, 4), 5, "shamir", 0.1, 1), ((6, 4, 2, 8), 12, "cosine", 0.02, 1),
-              ((4, 2, 2, 4), 1, "shamir", 0.05, 1)]
+              ((4, 2, 2, 4), 1, "shamir", 0.05, 1), ((2, 2, 4, 4), 32, "borici", 0.0, 1)]
 
 
 @pytest.mark.parametrize("dims,ns,kind,mq,sp", FULL_CASES)
