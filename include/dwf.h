@@ -113,7 +113,12 @@ typedef struct {
     int schur_target_pct; /* full system: the Schur residual aims at this percentage of tol
                           (<= 0 selects 50); a system whose full residual |eta - D psi| / |eta|
                           still misses tol continues once with a tightened target */
-    int reserved[4];
+    int use_x0;        /* warm start: sol holds an initial guess x0 on entry (Algorithm 2
+                          starting from x_hat = x0); the FP64 residual rhs - A x0 is solved
+                          for the correction, so the result meets tol relative to |rhs|.
+                          Normal system: x0's sites of the other parity are ignored.
+                          Right-hand sides of a batch are then solved one after another */
+    int reserved[3];
 } dwf_solve_params;
 
 /* kernel classes timed when params.profile != 0 */
@@ -315,6 +320,18 @@ dwf_status dwf_server_get_stats(dwf_server *srv, dwf_server_stats *stats);
  * only where delta would fall tens of orders below double precision, e.g. Ns = 64 on a
  * spectrum narrower than a factor of 2). */
 dwf_status dwf_optimal_weights(int Ns, double lambda_min, double lambda_max, double *omega, double *delta);
+
+/* Failure-detection hook, for tests.  Every wait of the hop kernels for a tile's TMA copies
+ * (an mbarrier phase) is bounded; when the bound runs out the kernel sets the context's
+ * error word, waits (again bounded) for the copy in flight and returns, and the call that
+ * launched it returns DWF_ETIMEOUT, clears the error word and leaves the context usable.
+ * wait_tries sets that bound in mbarrier polls (each poll suspends for a bounded,
+ * implementation-defined time, about 3.8 us on GB300; 0 restores the default 2^18, about
+ * one second).  skip_copies != 0 makes the
+ * hop kernels of this context issue no copies, so that nothing completes the barrier and
+ * every wait runs out; 0 restores normal operation.  Settings apply to later calls (a CUDA
+ * graph captured inside a solve takes them at capture).  Returns DWF_EINVAL for a null ctx. */
+dwf_status dwf_debug_set_wait(dwf_ctx *ctx, unsigned wait_tries, int skip_copies);
 
 /* Text of the last error on ctx ("" if none); valid until the next call on ctx. */
 const char *dwf_last_error(const dwf_ctx *ctx);

@@ -426,6 +426,8 @@ HopArgs hop_args(dwf_ctx *c, int prec, int outpar) {
   a.sc = c->d_sc;
   a.partials = c->d_part;
   a.ticket = c->d_ticket;
+  a.wait_tries = c->wait_tries;
+  a.skip_copies = c->skip_copies;
   return a;
 }
 
@@ -622,6 +624,13 @@ extern "C" {
 const char *dwf_status_string(dwf_status st) { return status_name(st); }
 
 const char *dwf_last_error(const dwf_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+dwf_status dwf_debug_set_wait(dwf_ctx *c, unsigned wait_tries, int skip_copies) {
+  if (!c) return DWF_EINVAL;
+  c->wait_tries = wait_tries ? wait_tries : kWaitTries;
+  c->skip_copies = skip_copies ? 1 : 0;
+  return DWF_OK;
+}
 
 void dwf_solve_params_default(dwf_solve_params *p) {
   if (!p) return;
@@ -1501,6 +1510,83 @@ dwf_status check_solve_args(dwf_ctx *c, dwf_solve_params *prm, const dwf_solve_p
   return DWF_OK;
 }
 
+// y = a + sb b on host-layout device arrays (sites of parity keep, all if keep < 0; the
+// rest set to 0) and |y|^2 into the scalar `fin`
+dwf_status host_axpy(dwf_ctx *c, cudaStream_t st, double *y, const double *a, const double *b, double sb, int keep,
+                     int fin) {
+  HostAxpyArgs v;
+  memset(&v, 0, sizeof(v));
+  v.y = y;
+  v.a = a;
+  v.b = b;
+  v.sb = sb;
+  v.g = geom(c);
+  v.keep = keep;
+  v.fin = fin;
+  v.sc = c->d_sc;
+  v.partials = c->d_part;
+  v.ticket = c->d_ticket;
+  Timed t(c, st, DWF_KC_F64);
+  CK(host_axpy_launch(v, c->sm_count, st));
+  return DWF_OK;
+}
+
+// Warm start (Algorithm 2 from a given x_hat): for each right-hand side the caller's sol
+// holds x0.  The FP64 residual r = rhs - A x0 of the requested system (A = D for the full
+// system, C C^dag on the Schur parity for the normal one) is solved for the correction,
+// A dx = r, to tol |rhs| / |r|, and sol = x0 + dx.  The residuals in the stats are then
+// relative to |rhs|.
+dwf_status warm_solve(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf_solve_params prm,
+                      dwf_solve_stats *S_out, cudaStream_t st) {
+  const bool full = prm.system == DWF_SYS_FULL;
+  const int keep = full ? -1 : prm.schur_parity;
+  const size_t nd = (size_t)c->V4 * c->Ns * 24;
+  void *pr, *pt, *pd;
+  TRY(get_raw(c, "warm_r", nd * sizeof(double), &pr));
+  TRY(get_raw(c, "warm_t", nd * sizeof(double), &pt));
+  TRY(get_raw(c, "warm_d", nd * sizeof(double), &pd));
+  double *r = static_cast<double *>(pr), *t = static_cast<double *>(pt), *dx = static_cast<double *>(pd);
+  dwf_solve_params inner = prm;
+  inner.use_x0 = 0;
+  dwf_status result = DWF_OK;
+  for (int k = 0; k < K; ++k) {
+    const double *rhs = d_rhs + (size_t)k * nd;
+    double *x = d_sol + (size_t)k * nd;
+    dwf_solve_stats &o = S_out[k];
+    memset(&o, 0, sizeof(o));
+    TRY(host_axpy(c, st, x, x, nullptr, 0.0, keep, FIN_NONE));  // x0 on the system's sites
+    TRY(dwf_apply_eo_dev(c, full ? DWF_OP_DFULL : DWF_OP_CCDAG, DWF_PREC_F64, prm.schur_parity, x, t, st));
+    TRY(host_axpy(c, st, r, rhs, nullptr, 0.0, keep, FIN_RED2));  // |rhs|^2
+    TRY(host_axpy(c, st, r, r, t, -1.0, keep, FIN_RED));          // r = rhs - A x0, |r|^2
+    TRY(pull_scalars(c, st));
+    const double bb = c->h_sc->red2, rr = c->h_sc->red;
+    o.inner_prec_used = prm.inner_prec;
+    o.mode_used = prm.mode == DWF_MODE_DEFECT ? DWF_MODE_DEFECT : DWF_MODE_RELIABLE;
+    if (bb == 0.0) {  // zero source: the solution is 0 (no site has parity 2)
+      TRY(host_axpy(c, st, x, x, nullptr, 0.0, 2, FIN_NONE));
+      o.converged = 1;
+      continue;
+    }
+    if (rr <= prm.tol * prm.tol * bb) {  // x0 already meets the tolerance
+      o.converged = 1;
+      o.true_res = sqrt(rr / bb);
+      o.true_res_full = full ? o.true_res : 0.0;
+      continue;
+    }
+    inner.tol = prm.tol * sqrt(bb / rr);
+    dwf_status s = solve_core(c, 1, r, dx, inner, &o, st);
+    if (s != DWF_OK && s != DWF_ENOCONV) return s;
+    if (s != DWF_OK && result == DWF_OK) result = s;
+    TRY(host_axpy(c, st, x, x, dx, 1.0, keep, FIN_NONE));
+    const double f = sqrt(rr / bb);
+    o.true_res *= f;
+    o.true_res_full *= f;
+  }
+  CK(cudaStreamSynchronize(st));
+  if (result != DWF_OK) return fail(c, result, "not converged");
+  return DWF_OK;
+}
+
 }  // namespace
 
 extern "C" dwf_status dwf_solve_batch_dev(dwf_ctx *c, int nrhs, const double *d_rhs, double *d_sol,
@@ -1518,6 +1604,7 @@ extern "C" dwf_status dwf_solve_batch_dev(dwf_ctx *c, int nrhs, const double *d_
     stats = local.data();
   }
   cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+  if (prm.use_x0) return warm_solve(c, nrhs, d_rhs, d_sol, prm, stats, st);
   return solve_core(c, nrhs, d_rhs, d_sol, prm, stats, st);
 }
 
@@ -1536,6 +1623,7 @@ extern "C" dwf_status dwf_solve_batch(dwf_ctx *c, int nrhs, const double *rhs, d
   TRY(get_raw(c, "host_in", full, &din));
   TRY(get_raw(c, "host_out", full, &dout));
   CK(cudaMemcpyAsync(din, rhs, full, cudaMemcpyHostToDevice, c->stream));
+  if (pp && pp->use_x0) CK(cudaMemcpyAsync(dout, sol, full, cudaMemcpyHostToDevice, c->stream));
   dwf_status s = dwf_solve_batch_dev(c, nrhs, (const double *)din, (double *)dout, pp, stats, c->stream);
   if (s != DWF_OK && s != DWF_ENOCONV) return s;
   CK(cudaMemcpyAsync(sol, dout, full, cudaMemcpyDeviceToHost, c->stream));

@@ -59,6 +59,10 @@ struct dwf_ctx {
   int sm_count = 0;
   int device = 0;
   long long launches = 0;
+  // failure-detection hook (dwf_debug_set_wait): bound of the hop kernels' waits for their
+  // TMA copies, and whether the copies are left out so that the waits run out
+  unsigned wait_tries = dwf::kWaitTries;
+  int skip_copies = 0;
   // profiling of the current call
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;

@@ -205,6 +205,7 @@ DWF_DECLARE_PREC(P_BF16)
 
 cudaError_t neighbours_launch(int *nbr, Geom g, int parity, int sm_count, cudaStream_t st);
 cudaError_t diff_norm2_launch(const VecArgs &v, int sm_count, cudaStream_t st);
+cudaError_t host_axpy_launch(const HostAxpyArgs &v, int sm_count, cudaStream_t st);
 cudaError_t point_sources_launch(double *rhs, long x0site, long V4, int Ns, cudaStream_t st);
 cudaError_t prop_extract_launch(const double *sol, double *prop, long V4, int Ns, int sm_count, cudaStream_t st);
 

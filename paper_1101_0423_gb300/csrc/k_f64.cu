@@ -26,4 +26,8 @@ cudaError_t diff_norm2_launch(const VecArgs &v, int sm_count, cudaStream_t st) {
   k_diff_norm2<<<vec_grid(v.n, sm_count), 256, 0, st>>>(v);
   return cudaGetLastError();
 }
+cudaError_t host_axpy_launch(const HostAxpyArgs &v, int sm_count, cudaStream_t st) {
+  k_host_axpy<<<vec_grid(2 * v.g.h * v.g.Ns * 24, sm_count), 256, 0, st>>>(v);
+  return cudaGetLastError();
+}
 }  // namespace dwf

@@ -39,7 +39,7 @@ class SolveParams(ctypes.Structure):
                 ("inner_prec", ctypes.c_int), ("mode", ctypes.c_int), ("system", ctypes.c_int),
                 ("schur_parity", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("profile", ctypes.c_int), ("stall_iters", ctypes.c_int),
-                ("schur_target_pct", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("schur_target_pct", ctypes.c_int), ("use_x0", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class SolveStats(ctypes.Structure):
@@ -127,6 +127,7 @@ def load(build_if_missing: bool = True):
         "dwf_poll": ([vp, ctypes.c_uint64, dp, ctypes.POINTER(Result)], i),
         "dwf_server_get_stats": ([vp, ctypes.POINTER(ServerStats)], i),
         "dwf_optimal_weights": ([i, d, d, dp, dp], i),
+        "dwf_debug_set_wait": ([vp, ctypes.c_uint, i], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -235,11 +236,14 @@ def _params(params=None, **kw) -> SolveParams:
     return p
 
 
-def dwf_solve(ctx, rhs, params=None, allow_noconv=False, **kw):
-    """Returns (solution array, stats dict).  Keyword arguments override params fields."""
+def dwf_solve(ctx, rhs, params=None, allow_noconv=False, x0=None, **kw):
+    """Returns (solution array, stats dict).  Keyword arguments override params fields; x0
+    (an initial guess, same layout as the solution) starts the solve from it (use_x0)."""
     rhs = _f64(rhs)
-    sol = np.empty_like(rhs)
+    sol = np.empty_like(rhs) if x0 is None else _f64(x0).copy()
     p = _params(params, **kw)
+    if x0 is not None:
+        p.use_x0 = 1
     stats = SolveStats()
     st = load().dwf_solve(ctx, _dp(rhs), _dp(sol), ctypes.byref(p), ctypes.byref(stats))
     if not (allow_noconv and st == DWF_ENOCONV):
@@ -257,12 +261,15 @@ def dwf_solve_dev(ctx, d_rhs, d_sol, params=None, stream=None, allow_noconv=Fals
     return stats.as_dict()
 
 
-def dwf_solve_batch(ctx, rhs, params=None, allow_noconv=False, **kw):
-    """rhs: array of shape (nrhs, 24*Ns*V4) (or flat).  Returns (solutions, list of stats dicts)."""
+def dwf_solve_batch(ctx, rhs, params=None, allow_noconv=False, x0=None, **kw):
+    """rhs: array of shape (nrhs, 24*Ns*V4) (or flat).  Returns (solutions, list of stats dicts).
+    x0: initial guesses of the same shape (use_x0)."""
     rhs = _f64(rhs)
     nrhs = rhs.shape[0] if rhs.ndim > 1 else 1
-    sol = np.empty_like(rhs)
+    sol = np.empty_like(rhs) if x0 is None else _f64(x0).reshape(rhs.shape).copy()
     p = _params(params, **kw)
+    if x0 is not None:
+        p.use_x0 = 1
     stats = (SolveStats * nrhs)()
     st = load().dwf_solve_batch(ctx, nrhs, _dp(rhs), _dp(sol), ctypes.byref(p), stats)
     if not (allow_noconv and st == DWF_ENOCONV):
@@ -294,6 +301,12 @@ def dwf_propagator(ctx, dims, x0, params=None, allow_noconv=False, **kw):
 
 def dwf_last_error(ctx) -> str:
     return load().dwf_last_error(ctx).decode()
+
+
+def dwf_debug_set_wait(ctx, wait_tries=0, skip_copies=False):
+    """Failure-detection hook: bound of the hop kernels' waits (mbarrier polls, 0 = default)
+    and whether their TMA copies are left out so that every wait runs out."""
+    _check(ctx, load().dwf_debug_set_wait(ctx, int(wait_tries), 1 if skip_copies else 0))
 
 
 class Context:

@@ -52,22 +52,24 @@ def test_struct_layouts_match_header(tmp_path):
     src.write_text('#include "dwf.h"\n#include <stdio.h>\n#include <stddef.h>\n'
                    'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(dwf_solve_params), sizeof(dwf_solve_stats),'
                    ' offsetof(dwf_solve_stats, kernel_launches), offsetof(dwf_solve_params, profile));'
-                   'printf("%zu\\n", offsetof(dwf_solve_params, schur_target_pct));return 0;}\n')
+                   'printf("%zu %zu\\n", offsetof(dwf_solve_params, schur_target_pct),'
+                   ' offsetof(dwf_solve_params, use_x0));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
-    sp, ss, off_kl, off_prof, off_pct = map(int, subprocess.check_output([str(exe)]).split())
+    sp, ss, off_kl, off_prof, off_pct, off_x0 = map(int, subprocess.check_output([str(exe)]).split())
     assert sp == ctypes.sizeof(dwf.SolveParams)
     assert ss == ctypes.sizeof(dwf.SolveStats)
     assert off_kl == dwf.SolveStats.kernel_launches.offset
     assert off_prof == dwf.SolveParams.profile.offset
     assert off_pct == dwf.SolveParams.schur_target_pct.offset
+    assert off_x0 == dwf.SolveParams.use_x0.offset
 
 
 def test_defaults_and_status_strings(lib):
     from paper_1101_0423_gb300 import dwf
     p = dwf.dwf_solve_params_default()
     assert p.tol == 1e-10 and p.inner_prec == dwf.PREC_F32 and p.schur_parity == 1
-    assert p.schur_target_pct == 50
+    assert p.schur_target_pct == 50 and p.use_x0 == 0
     assert lib.dwf_status_string(dwf.DWF_ENOCONV) == b"DWF_ENOCONV"
 
 
