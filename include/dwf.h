@@ -270,7 +270,8 @@ typedef struct {
     const double *sigma;    /* Ns weights, copied at submission */
     int gauge;              /* handle from dwf_server_add_gauge */
     const double *rhs;      /* host right-hand side (full-lattice host layout), copied */
-    dwf_solve_params params;/* solver settings (tol, system, inner_prec, ...) */
+    dwf_solve_params params;/* solver settings (tol, system, inner_prec, ...); use_x0 is
+                               ignored (a request carries no initial guess) */
 } dwf_request;
 
 typedef struct {

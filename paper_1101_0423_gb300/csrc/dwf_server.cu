@@ -278,6 +278,7 @@ dwf_status dwf_submit(dwf_server *srv, const dwf_request *req, uint64_t *ticket)
     }
   }
   job->req = *req;
+  job->req.params.use_x0 = 0;  // a request carries no initial guess
   job->omega.assign(req->omega, req->omega + req->Ns);
   job->sigma.assign(req->sigma, req->sigma + req->Ns);
   const size_t full = (size_t)req->dims[0] * req->dims[1] * req->dims[2] * req->dims[3] * req->Ns * 24;
