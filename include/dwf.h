@@ -235,8 +235,9 @@ dwf_status dwf_apply_eo_dev_static(dwf_ctx *ctx, int op, int prec, int parity, c
 /* Solve.  DWF_SYS_FULL: rhs = eta, sol = psi (full-lattice host arrays) with D psi = eta.
  * DWF_SYS_NORMAL: rhs = b, sol = x on the sites of params->schur_parity with
  * C C^dag x = b (other sites of sol are set to 0).  params may be NULL (defaults);
- * stats may be NULL.  Returns DWF_ENOCONV (with stats filled and the best x written)
- * when max_iter is reached first. */
+ * stats may be NULL.  With params->use_x0, sol holds the initial guess on entry (it is
+ * read, then overwritten with the solution).  Returns DWF_ENOCONV (with stats filled and
+ * the best x written) when max_iter is reached first. */
 dwf_status dwf_solve(dwf_ctx *ctx, const double *rhs, double *sol, const dwf_solve_params *params,
                      dwf_solve_stats *stats);
 /* Same with caller-owned device arrays, ordered on `stream`. */
