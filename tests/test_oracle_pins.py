@@ -430,3 +430,22 @@ def test_cg_iterates_are_the_krylov_galerkin_solutions(k):
     assert np.linalg.norm(xc - x_gal) / np.linalg.norm(x_gal) < 1e-10
     r = bc - A(xc)
     assert np.linalg.norm(Q.conj().T @ r) < 1e-10 * np.linalg.norm(r)
+
+
+def test_cg_error_decreases_monotonically_in_the_a_norm():
+    """A CG invariant: the A-norm of the error |x_k - x*|_A (A = C C^dag) falls strictly with
+    every iteration (x* from a solve to 1e-13)."""
+    dims, ns, mq, p = (2, 4, 2, 4), 4, 0.05, 0
+    U = inputs.gauge_field(dims, 0.5, seed=141)
+    om, sg = inputs.weights("borici", ns)
+    mp, mm = oracle.m5(ns, M0, mq, om, sg)
+    b = inputs.gaussian_source(dims, ns, seed=142, parity=p)
+    xs, _, rr = oracle.cg(dims, ns, U, mp, mm, p, b, tol=1e-13, maxiter=3000)
+    assert rr < 1e-13
+    prev = np.inf
+    for k in range(1, 16):
+        x, iters, _ = oracle.cg(dims, ns, U, mp, mm, p, b, tol=1e-300, maxiter=k)
+        e = x - xs
+        ea = np.sqrt(oracle.dot(e, oracle.ccdag_op(dims, ns, U, mp, mm, p, e)).real)
+        assert iters == k and ea < prev
+        prev = ea
