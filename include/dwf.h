@@ -309,8 +309,8 @@ dwf_status dwf_poll(dwf_server *srv, uint64_t ticket, double *psi_out, dwf_resul
 /* Latency percentiles, throughput and occupancy of the server so far. */
 dwf_status dwf_server_get_stats(dwf_server *srv, dwf_server_stats *stats);
 
-/* Weights of the optimal domain-wall operator (sigma = omega in Eq. 1; Sec. 2.1 takes them
- * "such that the maximal chiral symmetry is attained" from a formula it only cites).
+/* Weights of the optimal domain-wall operator (sigma = omega in Eq. 1; Sec. 2.1 wants the
+ * best chiral symmetry Ns slices allow and takes them from a cited formula it does not print).
  * Reading: the omega_s that make S(lam) = (1 - T)/(1 + T), T = prod_s (1 - omega_s lam) /
  * (1 + omega_s lam), the best uniform approximation of sgn(lam) on [lambda_min, lambda_max],
  * the range of |H_w| = |g5 D_w| the caller supplies; computed by the Remez exchange (the

@@ -6,8 +6,9 @@ operator reduces, in four dimensions, to one built on the sign-function approxim
 
     S(lam) = (1 - T(lam)) / (1 + T(lam)),   T(lam) = prod_s (1 - omega_s lam) / (1 + omega_s lam),
 
-with lam over the spectrum [lmin, lmax] of |H_w|.  Sec. 2.1 takes the weights "such that
-the maximal chiral symmetry is attained" from a formula it only cites.  Reading: the
+with lam over the spectrum [lmin, lmax] of |H_w|.  Sec. 2.1 names the goal of these weights
+(chiral symmetry as good as Ns slices allow) and takes them from a cited formula that it
+does not print.  Reading: the
 optimal weights make S the best uniform approximation of sgn on [lmin, lmax], i.e. they
 minimize delta = max |1 - S(lam)|.  By the alternation theorem the error e = 1 - S of the
 optimum takes the value +-delta, with alternating signs, at Ns + 1 points.

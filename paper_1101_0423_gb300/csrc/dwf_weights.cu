@@ -2,9 +2,9 @@
 //
 // With sigma = omega, Eq. 1 reduces in four dimensions to an operator built on
 //   S(lam) = (1 - T(lam)) / (1 + T(lam)),  T(lam) = prod_s (1 - omega_s lam) / (1 + omega_s lam)
-// over the spectrum [lmin, lmax] of |H_w|.  The paper takes its weights "such that the
-// maximal chiral symmetry is attained" from a formula it cites (Sec. 2.1); the reading
-// here is the best uniform approximation of sgn: omega minimizing max |1 - S| on
+// over the spectrum [lmin, lmax] of |H_w|.  Sec. 2.1 wants the weights that give the best
+// chiral symmetry Ns slices allow and takes them from a cited formula it does not print;
+// the reading here is the best uniform approximation of sgn: omega minimizing max |1 - S| on
 // [lmin, lmax].  The optimum is characterised by alternation (the error e = 1 - S reaches
 // +-delta with alternating signs at Ns + 1 points), which the Remez exchange below solves:
 //   1. with x_s = 1 / omega_s the zeros of T, solve e(lam_i) = (-1)^i delta at the
