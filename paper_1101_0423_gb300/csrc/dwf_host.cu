@@ -1,8 +1,8 @@
 // dwf_host.cu -- C-ABI entry points: context, gauge, operator applications, solver.
 //
-// The host does the flow control (Sec. 3: "CPU (host) is used to do the flow control,
-// memory assignment, and device control"); every vector operation, reduction and
-// operator application runs in the kernels of dwf_kernels.cuh.  The CG scalars
+// As in Sec. 3, the host only steers: it decides what runs next, owns the allocations and
+// drives the device; every vector operation, reduction and operator application runs in
+// the kernels of dwf_kernels.cuh.  The CG scalars
 // (alpha, beta, |r|^2, restart flag) stay on the device; the host reads them once per
 // batch of inner iterations, and a batch is replayed from a CUDA graph.
 #include <math.h>
