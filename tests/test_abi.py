@@ -104,3 +104,8 @@ def test_create_builds_the_m5_recurrence_for_any_valid_weights(lib, ns, kind, mq
         assert e.status != dwf.DWF_EINVAL, "recurrence tables disagree with the dense M5"
     else:
         dwf.dwf_destroy(h)
+
+
+def test_debug_wait_hook_rejects_a_null_context(lib):
+    from paper_1101_0423_gb300 import dwf
+    assert lib.dwf_debug_set_wait(None, 0, 1) == dwf.DWF_EINVAL
