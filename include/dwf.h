@@ -117,6 +117,7 @@ typedef struct {
                           starting from x_hat = x0); the FP64 residual rhs - A x0 is solved
                           for the correction, so the result meets tol relative to |rhs|.
                           Normal system: x0's sites of the other parity are ignored.
+                          A source or guess with a non-finite entry gives DWF_EINVAL.
                           Right-hand sides of a batch are then solved one after another */
     int reserved[3];
 } dwf_solve_params;

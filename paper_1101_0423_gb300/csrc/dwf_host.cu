@@ -1560,6 +1560,7 @@ dwf_status warm_solve(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
     TRY(host_axpy(c, st, r, r, t, -1.0, keep, FIN_RED));          // r = rhs - A x0, |r|^2
     TRY(pull_scalars(c, st));
     const double bb = c->h_sc->red2, rr = c->h_sc->red;
+    if (!std::isfinite(bb) || !std::isfinite(rr)) return fail(c, DWF_EINVAL, "source or initial guess is not finite");
     o.inner_prec_used = prm.inner_prec;
     o.mode_used = prm.mode == DWF_MODE_DEFECT ? DWF_MODE_DEFECT : DWF_MODE_RELIABLE;
     if (bb == 0.0) {  // zero source: the solution is 0 (no site has parity 2)
