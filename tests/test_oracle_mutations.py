@@ -33,7 +33,8 @@ MUTATIONS = [
      [lambda: pins.test_free_field_momentum_closed_form((4, 6, 2, 8))]),
     ("corner of L+ sign", "else Lp[(s - 1) * Ns + (Ns - 1)] += -mq / (2.0 * m0);",
      "else Lp[(s - 1) * Ns + (Ns - 1)] += mq / (2.0 * m0);",
-     [lambda: pins.test_m5_shamir_closed_form(4, 0.05), pins.test_lmat_is_eq4]),
+     [lambda: pins.test_m5_shamir_closed_form(4, 0.05), pins.test_lmat_is_eq4,
+      lambda: pins.test_m5_borici_spectrum(4, 0.4)]),
     ("chiralities swapped", "spin < 2 ? Mp : Mm", "spin < 2 ? Mm : Mp",
      [lambda: pins.test_dfull_matches_dense_assembly((2, 2, 2, 4), 3, "cosine")]),
     ("c applied on the column side", "A[i * Ns + j] = (i == j ? 1.0 : 0.0) + c_i * L[i * Ns + j];",

@@ -192,6 +192,26 @@ def test_m5_shamir_closed_form(ns, mq):
     assert np.max(np.abs(mm - want.T)) < 1e-15
 
 
+@pytest.mark.parametrize("ns", [3, 4, 8, 16])
+@pytest.mark.parametrize("mq", [0.05, 0.4])
+def test_m5_borici_spectrum(ns, mq):
+    """Borici (sigma = omega = 1, so c = 1): Eq. 8 reads M5 = [(4 - m0) + (1 - L)(1 + L)^{-1}]^{-1}.
+    L+ shifts s up by one and wraps with the factor kappa = -mq/(2 m0) (Eq. 4), so
+    L+^Ns = kappa and its eigenvalues are the Ns roots lam of lam^Ns = kappa; M5+ then has
+    the eigenvalues 1 / [(4 - m0) + (1 - lam)/(1 + lam)], and M5- = M5+^T the same."""
+    om, sg = inputs.weights("borici", ns)
+    mp, mm = oracle.m5(ns, M0, mq, om, sg)
+    kappa = -mq / (2 * M0)
+    lam = abs(kappa) ** (1.0 / ns) * np.exp(1j * np.pi * (2 * np.arange(ns) + 1) / ns)  # kappa < 0
+    want = 1.0 / ((4 - M0) + (1 - lam) / (1 + lam))
+    for m in (mp, mm):
+        got = np.linalg.eigvals(m)
+        # match each predicted eigenvalue to the nearest computed one (a permutation)
+        d = np.abs(got[:, None] - want[None, :])
+        assert np.all(np.sort(d.min(axis=0)) < 1e-12)
+        assert sorted(np.argmin(d, axis=0)) == list(range(ns))
+
+
 def test_lmat_is_eq4():
     lp, lm = oracle.lmat(5, M0, 0.07)
     want = np.zeros((5, 5))
