@@ -100,6 +100,34 @@ def test_free_5d_operator_momentum_block(dims, ns):
         assert rel(out, phase[:, None, None, None] * block[None]) < 1e-13
 
 
+@pytest.mark.parametrize("p_sch", [0, 1])
+def test_free_field_solve_is_the_inverse_momentum_block(p_sch):
+    """U = 1, eta = e^{ipx} chi: the even-odd solve of Eq. 10 (source preparation, CG on
+    C C^dag, reconstruction) must return e^{ipx} D(p)^{-1} chi, with D(p) the 4Ns x 4Ns
+    momentum block of Eq. 1 (per colour), inverted here with numpy."""
+    dims, ns, mq = (4, 2, 2, 4), 4, 0.05
+    U = inputs.unit_gauge(dims)
+    g = dense.gammas()[0]
+    coords = np.array(dense.coords(dims))
+    rng = np.random.default_rng(19)
+    om, sg = rng.uniform(0.6, 1.4, ns), rng.uniform(-0.3, 0.8, ns)
+    Lp, Lm = eq4_l(ns, mq)
+    P = [np.diag([1, 1, 0, 0]).astype(complex), np.diag([0, 0, 1, 1]).astype(complex)]
+    Lfull = np.kron(Lp, P[0]) + np.kron(Lm, P[1])          # (s, spin) x (s', spin')
+    W = np.kron(np.diag(om), np.eye(4)) + np.diag(np.repeat(sg, 4)) @ Lfull
+    for n in [(1, 0, 0, 1), (0, 1, 1, 3)]:
+        p = 2 * np.pi * np.array(n) / np.array(dims)
+        Dp = (4 - M0 - np.cos(p).sum()) * np.eye(4) + 1j * sum(g[mu] * np.sin(p[mu]) for mu in range(4))
+        block = np.kron(np.eye(ns), Dp) @ W + np.eye(4 * ns) - Lfull
+        chi = rng.normal(size=(ns, 4, 3)) + 1j * rng.normal(size=(ns, 4, 3))
+        phase = np.exp(1j * coords @ p)
+        eta = (phase[:, None, None, None] * chi[None]).view(np.float64).reshape(-1)
+        psi, _, relres = oracle.solve_full(dims, ns, U, M0, mq, om, sg, eta, p=p_sch, tol=1e-13)
+        want = np.linalg.solve(block, chi.reshape(4 * ns, 3)).reshape(ns, 4, 3)
+        assert relres < 1e-12
+        assert rel(cview(psi, dims, ns), phase[:, None, None, None] * want[None]) < 1e-10
+
+
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 4, 6, 4)])
 def test_gamma5_hermiticity_of_dw(dims):
     """<chi, g5 D_w g5 psi> = <D_w chi, psi> for a random gauge field."""
