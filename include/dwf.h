@@ -288,6 +288,7 @@ typedef struct {
     double p50_ms, p99_ms, mean_ms;  /* latency (submission to completion) of completed requests */
     double solves_per_s;             /* completed / (last completion - first submission) */
     double hbm_reserved_gb;          /* device-memory estimate of the admitted contexts */
+    long long cancelled;             /* requests withdrawn by dwf_cancel before admission */
 } dwf_server_stats;
 
 void dwf_server_params_default(dwf_server_params *p);
@@ -307,6 +308,14 @@ dwf_status dwf_submit(dwf_server *srv, const dwf_request *req, uint64_t *ticket)
  * ticket and returns DWF_OK (the solve's own status is result->status).  DWF_EINVAL for an
  * unknown ticket. */
 dwf_status dwf_poll(dwf_server *srv, uint64_t ticket, double *psi_out, dwf_result *result);
+/* Withdraw a request that is still queued: DWF_OK (its ticket is released; a later poll
+ * returns DWF_EINVAL), DWF_EBUSY if a worker has already taken it (poll it as usual),
+ * DWF_EINVAL for an unknown ticket. */
+dwf_status dwf_cancel(dwf_server *srv, uint64_t ticket);
+/* Open (nonzero) or close admission: while closed, submitted requests queue but no worker
+ * admits one (running solves continue), e.g. to drain the device or to stage a burst of
+ * requests.  Servers start open. */
+dwf_status dwf_server_set_admission(dwf_server *srv, int open);
 /* Latency percentiles, throughput and occupancy of the server so far. */
 dwf_status dwf_server_get_stats(dwf_server *srv, dwf_server_stats *stats);
 

@@ -93,7 +93,8 @@ struct dwf_server {
   size_t reserved = 0;
   uint64_t next_ticket = 1;
   bool stop = false;
-  long long submitted = 0, completed = 0, in_flight = 0;
+  bool admit = true;  // dwf_server_set_admission: queued requests wait while false
+  long long submitted = 0, completed = 0, in_flight = 0, cancelled = 0;
   std::vector<double> latencies;
   Clock::time_point first_submit, last_done;
   bool any_submit = false;
@@ -110,7 +111,7 @@ void dwf_server::worker_loop() {
   for (;;) {
     Job *job = nullptr;
     while (!stop) {
-      if (!queue.empty()) {
+      if (admit && !queue.empty()) {
         Job *head = queue.front();
         const bool reuse = ctx && head->key == ctx_key;
         // a context not reused by the head request is released before admission
@@ -323,11 +324,40 @@ dwf_status dwf_poll(dwf_server *srv, uint64_t ticket, double *psi_out, dwf_resul
   return DWF_OK;
 }
 
+dwf_status dwf_cancel(dwf_server *srv, uint64_t ticket) {
+  if (!srv) return DWF_EINVAL;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->jobs.find(ticket);
+  if (it == srv->jobs.end()) return DWF_EINVAL;
+  Job *job = it->second;
+  // a queued job is only ever touched under the lock, so it can go; one that a worker has
+  // taken runs to completion
+  auto q = std::find(srv->queue.begin(), srv->queue.end(), job);
+  if (q == srv->queue.end()) return DWF_EBUSY;
+  srv->queue.erase(q);
+  srv->jobs.erase(it);
+  delete job;
+  ++srv->cancelled;
+  srv->cv.notify_all();  // the next request may now be admissible
+  return DWF_OK;
+}
+
+dwf_status dwf_server_set_admission(dwf_server *srv, int open) {
+  if (!srv) return DWF_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->admit = open != 0;
+  }
+  srv->cv.notify_all();
+  return DWF_OK;
+}
+
 dwf_status dwf_server_get_stats(dwf_server *srv, dwf_server_stats *out) {
   if (!srv || !out) return DWF_EINVAL;
   std::lock_guard<std::mutex> lk(srv->mu);
   memset(out, 0, sizeof(*out));
   out->submitted = srv->submitted;
+  out->cancelled = srv->cancelled;
   out->completed = srv->completed;
   out->in_flight = srv->in_flight;
   out->queued = (long long)srv->queue.size();

@@ -79,7 +79,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
                 ("in_flight", ctypes.c_longlong), ("queued", ctypes.c_longlong),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
-                ("solves_per_s", ctypes.c_double), ("hbm_reserved_gb", ctypes.c_double)]
+                ("solves_per_s", ctypes.c_double), ("hbm_reserved_gb", ctypes.c_double),
+                ("cancelled", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -128,6 +129,8 @@ def load(build_if_missing: bool = True):
         "dwf_server_get_stats": ([vp, ctypes.POINTER(ServerStats)], i),
         "dwf_optimal_weights": ([i, d, d, dp, dp], i),
         "dwf_debug_set_wait": ([vp, ctypes.c_uint, i], i),
+        "dwf_cancel": ([vp, ctypes.c_uint64], i),
+        "dwf_server_set_admission": ([vp, i], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -396,6 +399,20 @@ def dwf_poll(srv, ticket, out=None):
         raise DwfError(st, "dwf_poll")
     return out, {"status": res.status, "stats": res.stats.as_dict(), "queue_ms": res.queue_ms,
                  "latency_ms": res.latency_ms}
+
+
+def dwf_cancel(srv, ticket) -> bool:
+    """Withdraw a queued request: True if it was withdrawn, False if a worker already took it."""
+    st = load().dwf_cancel(srv, ctypes.c_uint64(ticket))
+    if st == DWF_EBUSY:
+        return False
+    if st != DWF_OK:
+        raise DwfError(st, "dwf_cancel")
+    return True
+
+
+def dwf_server_set_admission(srv, open_: bool):
+    _check(None, load().dwf_server_set_admission(srv, 1 if open_ else 0))
 
 
 def dwf_server_get_stats(srv) -> dict:

@@ -98,3 +98,63 @@ def test_without_device_the_failure_reaches_poll(dwf):
         assert st["completed"] == 3 and st["in_flight"] == 0 and st["hbm_reserved_gb"] == 0
     finally:
         dwf.dwf_server_destroy(srv)
+
+
+def _wait(dwf, srv, tickets, timeout=60):
+    done = {}
+    t0 = time.time()
+    while len(done) < len(tickets) and time.time() - t0 < timeout:
+        for t in tickets:
+            if t not in done:
+                r = dwf.dwf_poll(srv, t)
+                if r is not None:
+                    done[t] = r[1]
+        time.sleep(0.01)
+    return done
+
+
+def test_cancel_withdraws_a_queued_request(dwf):
+    """With admission closed, requests queue; a queued one can be withdrawn (its ticket is
+    gone), the others run once admission opens, and a finished one can no longer be
+    withdrawn.  Host logic only: without a GPU the admitted solves end with DWF_ECUDA."""
+    srv = dwf.dwf_server_create(hbm_budget_gb=2.0, max_inflight=2)
+    try:
+        g = dwf.dwf_server_add_gauge(srv, DIMS, inputs.unit_gauge(DIMS))
+        om, sg, rhs = _req_args()
+        dwf.dwf_server_set_admission(srv, False)
+        t = [dwf.dwf_submit(srv, DIMS, NS, 1.8, 0.05, om, sg, g, rhs) for _ in range(3)]
+        time.sleep(0.05)
+        st = dwf.dwf_server_get_stats(srv)
+        assert st["queued"] == 3 and st["in_flight"] == 0 and st["completed"] == 0
+        assert dwf.dwf_cancel(srv, t[1]) is True
+        for call in (lambda: dwf.dwf_cancel(srv, t[1]), lambda: dwf.dwf_poll(srv, t[1])):
+            with pytest.raises(dwf.DwfError) as e:
+                call()
+            assert e.value.status == dwf.DWF_EINVAL
+        st = dwf.dwf_server_get_stats(srv)
+        assert st["queued"] == 2 and st["cancelled"] == 1 and st["submitted"] == 3
+        dwf.dwf_server_set_admission(srv, True)
+        t0 = time.time()
+        while dwf.dwf_server_get_stats(srv)["completed"] < 2 and time.time() - t0 < 60:
+            time.sleep(0.01)
+        assert dwf.dwf_cancel(srv, t[0]) is False  # finished, not yet collected
+        done = _wait(dwf, srv, [t[0], t[2]])
+        assert len(done) == 2
+        want = dwf.DWF_OK if has_gpu() else dwf.DWF_ECUDA
+        assert all(r["status"] == want for r in done.values())
+        st = dwf.dwf_server_get_stats(srv)
+        assert st["completed"] == 2 and st["queued"] == 0 and st["cancelled"] == 1
+    finally:
+        dwf.dwf_server_destroy(srv)
+
+
+def test_cancel_rejects_unknown_tickets_and_null_servers(dwf):
+    srv = dwf.dwf_server_create(hbm_budget_gb=1.0, max_inflight=1)
+    try:
+        with pytest.raises(dwf.DwfError) as e:
+            dwf.dwf_cancel(srv, 999)
+        assert e.value.status == dwf.DWF_EINVAL
+    finally:
+        dwf.dwf_server_destroy(srv)
+    assert dwf.load().dwf_cancel(None, 1) == dwf.DWF_EINVAL
+    assert dwf.load().dwf_server_set_admission(None, 1) == dwf.DWF_EINVAL
