@@ -109,3 +109,19 @@ def test_create_builds_the_m5_recurrence_for_any_valid_weights(lib, ns, kind, mq
 def test_debug_wait_hook_rejects_a_null_context(lib):
     from paper_1101_0423_gb300 import dwf
     assert lib.dwf_debug_set_wait(None, 0, 1) == dwf.DWF_EINVAL
+
+
+def test_server_struct_layouts_match_header(tmp_path):
+    from paper_1101_0423_gb300 import dwf
+    src = tmp_path / "sz2.c"
+    src.write_text('#include "dwf.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(dwf_server_params),'
+                   ' sizeof(dwf_request), sizeof(dwf_result), sizeof(dwf_server_stats),'
+                   ' offsetof(dwf_server_stats, cancelled), offsetof(dwf_request, params));return 0;}\n')
+    exe = tmp_path / "sz2"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    sp, rq, rs, ss, off_c, off_p = map(int, subprocess.check_output([str(exe)]).split())
+    assert sp == ctypes.sizeof(dwf.ServerParams)
+    assert rq == ctypes.sizeof(dwf.Request) and off_p == dwf.Request.params.offset
+    assert rs == ctypes.sizeof(dwf.Result)
+    assert ss == ctypes.sizeof(dwf.ServerStats) and off_c == dwf.ServerStats.cancelled.offset
