@@ -18,7 +18,8 @@ points solve e(lam_i) = (-1)^i delta for the Ns zeros x_s = 1 / omega_s of T and
 (scipy's root finder, in the zeros' logarithms); move each reference point to the extremum of |e|
 between consecutive zeros, located on a dense logarithmic grid and refined by a bounded
 1-D maximisation; repeat until the extrema agree.  Parity pins (tests/test_optimal_weights.py):
-the closed form for Ns = 1, the alternation of the result, local optimality against
+Zolotarev's closed-form solution in Jacobi elliptic functions (S(lam) and delta agree), the
+closed form for Ns = 1, the alternation of the result, local optimality against
 perturbations, and delta decreasing with Ns.
 """
 from __future__ import annotations

@@ -7,7 +7,7 @@ best uniform approximation of sgn on [lmin, lmax].  Pins: the closed form for Ns
 (S = omega lam, so omega = 2/(lmin + lmax) and delta = (lmax - lmin)/(lmax + lmin)); the
 alternation theorem (the error 1 - S reaches +-delta with alternating signs at exactly
 Ns + 1 points); local optimality (no perturbation of the weights lowers max |1 - S|); and
-delta falling as Ns grows.
+delta falling as Ns grows; and Zolotarev's closed-form solution in elliptic functions.
 """
 import numpy as np
 import pytest
@@ -59,6 +59,58 @@ def test_no_perturbation_lowers_the_deviation(ns, lmin, lmax):
         trial = om * np.exp(1e-3 * rng.standard_normal(ns))
         _, e = dense_error(trial, lmin, lmax, 100001)
         assert np.max(np.abs(e)) > d * (1 - 1e-9)
+
+
+def zolotarev(ns, lmin, lmax):
+    """Zolotarev's solution, in elliptic functions, written independently of the oracle's
+    Remez exchange.  Among T(lam) = prod_j (p_j - lam)/(p_j + lam), the one of least
+    max |T| on [lmin, lmax] has the zeros p_j = lmax dn((2j - 1) K / (2 Ns), k), with modulus
+    k^2 = 1 - (lmin/lmax)^2 and K = K(k) (Zolotarev's third problem, the same minimax as
+    the optimal shifts of the ADI iteration); |T| then equioscillates with T(lmin) = delta_T.
+    S_T = (1 - T)/(1 + T) spans [m, 1/m], m = (1 - delta_T)/(1 + delta_T), so the multiple
+    C S_T with C = 2 m / (1 + m^2) spans [1 - delta, 1 + delta], delta = 2 delta_T/(1 + delta_T^2),
+    touching both ends at the Ns + 1 alternation points: the best uniform approximation of
+    sgn in the (1 - T)/(1 + T) family (a constant multiple of an odd rational of this type is
+    again of this type).  Returns (S as a function of lam, delta)."""
+    from scipy import special
+    m_par = 1.0 - (lmin / lmax) ** 2                     # scipy takes the parameter k^2
+    u = (2 * np.arange(1, ns + 1) - 1) * special.ellipk(m_par) / (2 * ns)
+    p = lmax * special.ellipj(u, m_par)[2]               # dn
+    def T(lam):
+        lam = np.atleast_1d(np.asarray(lam, dtype=np.float64))
+        return np.prod((p - lam[:, None]) / (p + lam[:, None]), axis=1)
+    dT = abs(T(lmin)[0])
+    m = (1.0 - dT) / (1.0 + dT)
+    C = 2.0 * m / (1.0 + m * m)
+    return (lambda lam: C * (1.0 - T(lam)) / (1.0 + T(lam))), 2.0 * dT / (1.0 + dT * dT)
+
+
+@pytest.mark.parametrize("ns,lmin,lmax", [(1, 0.05, 6.0), (4, 0.05, 6.2), (8, 0.05, 6.2), (8, 0.02, 7.0),
+                                          (16, 0.05, 6.2), (16, 0.3, 2.0), (5, 0.1, 5.0)])
+def test_oracle_matches_zolotarev_closed_form(ns, lmin, lmax):
+    """The oracle's weights give the same S(lam) and delta as Zolotarev's closed form (the
+    best approximation is unique, so equal S on the interval fixes the weights)."""
+    S_z, d_z = zolotarev(ns, lmin, lmax)
+    om, d = W.optimal_weights(ns, lmin, lmax)
+    g = np.exp(np.linspace(np.log(lmin), np.log(lmax), 100001))
+    assert d == pytest.approx(d_z, rel=1e-9)
+    assert np.max(np.abs((1.0 - W.error(om, g)) - S_z(g))) < 1e-10
+
+
+def test_zolotarev_closed_form_alternates():
+    """Check on the closed form itself: its error reaches +-delta with alternating signs at
+    Ns + 1 points (a mistyped modulus or argument of dn would break this)."""
+    ns, lmin, lmax = 8, 0.05, 6.2
+    S_z, d_z = zolotarev(ns, lmin, lmax)
+    g = np.exp(np.linspace(np.log(lmin), np.log(lmax), 400001))
+    e = 1.0 - S_z(g)
+    assert np.max(np.abs(e)) == pytest.approx(d_z, rel=1e-9)
+    sign = np.sign(e)
+    cuts = np.flatnonzero(sign[1:] != sign[:-1])
+    assert len(cuts) == ns
+    bounds = np.concatenate([[0], cuts + 1, [len(g)]])
+    peaks = np.array([e[a:b][np.argmax(np.abs(e[a:b]))] for a, b in zip(bounds[:-1], bounds[1:])])
+    assert np.allclose(np.abs(peaks), d_z, rtol=1e-6)
 
 
 def test_deviation_falls_with_ns():
