@@ -36,10 +36,10 @@ METRIC = "CG Gflops & % HBM roofline (16^3x32,Ns16); served solves/s, p99 latenc
 PAPER_BEST_GFLOPS = 233.0  # GTX 480, CG (mixed), same lattice (Table 1): other hardware, context
 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch, bytes, of the
-# FP32 kernel classes at this workload, from profiles/k_hop_f32_16x16x16x32_Ns16.md.  It is
-# valid only for the kernel source it was captured on; clear it when k_hop changes.
-NCU_TRAFFIC = {"hop_m5": 151052544 + 66592000, "hop_xpay": 251834880 + 74691072,
-               "hop_update": 352654848 + 77566208, "smix_p": 302054656 + 241717504}
+# FP32 kernel classes at this workload, from one ncu capture of the kernels as they stand
+# (summarised under profiles/).  Valid only for the kernel source it was captured on: empty
+# (traffic reported as null) until the kernels are captured again after a change.
+NCU_TRAFFIC = {}
 
 
 def flops_ccdag(n, ns):

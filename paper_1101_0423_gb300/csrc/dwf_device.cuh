@@ -30,23 +30,28 @@ namespace dwf {
 enum { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3 };
 
 template <int P> struct PT;
+// LREALS: reals per link; SITE_LREALS: reals per site's eight links, padding included
 template <> struct PT<P_F64> {
   using real = double; using chunk = double2; using lreal = double;
-  static constexpr int NCH = 12, RPC = 2, LREALS = 18; static constexpr bool HALF = false;
+  static constexpr int NCH = 12, RPC = 2, LREALS = 18, SITE_LREALS = 8 * 18; static constexpr bool HALF = false;
 };
 template <> struct PT<P_F32> {
   using real = float; using chunk = float4; using lreal = float;
-  // links padded to 20 reals (80 bytes) so that the nine complex entries load as five float4
-  static constexpr int NCH = 6, RPC = 4, LREALS = 20; static constexpr bool HALF = false;
+  // links padded to 20 reals (80 bytes) so that the nine complex entries load as five float4;
+  // a site's eight links padded by 16 bytes to 656 (41 float4), so that sites adjacent in a
+  // half-warp read their broadcast link entries from different bank groups
+  static constexpr int NCH = 6, RPC = 4, LREALS = 20, SITE_LREALS = 8 * 20 + 4; static constexpr bool HALF = false;
 };
 template <> struct PT<P_F16> {
   using real = float; using chunk = uint4; using lreal = __half;
-  static constexpr int NCH = 3, RPC = 8, LREALS = 12; static constexpr bool HALF = true;
+  static constexpr int NCH = 3, RPC = 8, LREALS = 12, SITE_LREALS = 8 * 12; static constexpr bool HALF = true;
 };
 template <> struct PT<P_BF16> {
   using real = float; using chunk = uint4; using lreal = __nv_bfloat16;
-  static constexpr int NCH = 3, RPC = 8, LREALS = 12; static constexpr bool HALF = true;
+  static constexpr int NCH = 3, RPC = 8, LREALS = 12, SITE_LREALS = 8 * 12; static constexpr bool HALF = true;
 };
+// float4 per site of the FP32 link form the hop reads (as stored, or expanded from 16 bits)
+constexpr int LINK_SITE_F4 = 41;
 
 struct Field {
   void *v;

@@ -399,7 +399,11 @@ cudaError_t gauge_any(int prec, const double *U, void *G, Geom g, int par, int s
 }
 
 size_t link_bytes_per_site(int prec) {
-  return prec == P_F64 ? 8 * 18 * 8 : prec == P_F32 ? 8 * 20 * 4 : 8 * 12 * 2;
+  switch (prec) {
+    case P_F64: return PT<P_F64>::SITE_LREALS * sizeof(double);
+    case P_F32: return PT<P_F32>::SITE_LREALS * sizeof(float);
+    default: return PT<P_F16>::SITE_LREALS * 2;
+  }
 }
 
 // doubled gauge field of precision prec, built on first use
@@ -1684,57 +1688,23 @@ extern "C" dwf_status dwf_propagator(dwf_ctx *c, const int x0[4], const dwf_solv
 // ====================================================================== allocation-free variant
 //
 // dwf_apply_eo_dev_static is dwf_apply_eo_dev for the Schur-parity operators with every
-// work field (packed input and output, three intermediates) and the reduction scratch
-// (block partial sums and the last-block ticket) taken from one static device array, so a
-// call never allocates.  It is for callers that must not allocate device memory while
-// they run: code recording a CUDA stream capture (cudaMalloc is not allowed while a
-// capture is open), applications whose device memory is owned by their own pool
-// allocator or held to a fixed budget, and latency-critical paths where a first-call
-// allocation would stall.  The array is a file-scope __device__ variable, so every GPU
-// that loads the library holds it until the process exits.
-
-#include <mutex>
+// work field (packed input and output, three intermediates), the CG scalar block and the
+// reduction scratch (block partial sums and the last-block ticket) taken from one static
+// device array, so a call never allocates.  It is for callers that cannot let a library
+// allocate device memory: applications whose device memory is owned by their own pool
+// allocator (a framework's caching allocator that already holds the GPU's memory) or held
+// to a fixed budget decided at start-up, and paths that must not meet the device-wide
+// synchronisation a cudaMalloc or cudaFree can bring.  The array is a file-scope
+// __device__ variable, so every GPU that loads the library holds it until the process
+// exits.  The call touches no mutable state of the context (its device address of the
+// array aside), so other work on the same context is not redirected to the array.
 
 namespace {
 
 constexpr size_t kStaticScratchBytes = (size_t)64 << 20;  // 64 MiB per device
 __device__ __align__(256) unsigned char g_dwf_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxStaticDevices = 256;
-void *g_static_scratch_addr[kMaxStaticDevices] = {};
-std::mutex g_static_scratch_mutex;
-
-// Device address of the static array on device `dev` (which must be current).  In host
-// code the array's name is only a host-side stand-in, so the address is looked up once per
-// device with cudaGetSymbolAddress and cached.
-cudaError_t static_scratch_address(int dev, void **out) {
-  std::lock_guard<std::mutex> lock(g_static_scratch_mutex);
-  if (!g_static_scratch_addr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_dwf_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_static_scratch_addr[dev] = p;
-  }
-  *out = g_static_scratch_addr[dev];
-  return cudaSuccess;
-}
-
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
-
-// points the context's reduction scratch at the static array for the duration of one call
-struct ReductionScratchSwap {
-  dwf_ctx *c;
-  double *part;
-  unsigned *ticket;
-  ReductionScratchSwap(dwf_ctx *c_, double *p, unsigned *t) : c(c_), part(c_->d_part), ticket(c_->d_ticket) {
-    c->d_part = p;
-    c->d_ticket = t;
-  }
-  ~ReductionScratchSwap() {
-    c->d_part = part;
-    c->d_ticket = ticket;
-  }
-};
 
 }  // namespace
 
@@ -1756,22 +1726,29 @@ extern "C" dwf_status dwf_apply_eo_dev_static(dwf_ctx *c, int op, int prec, int 
     return fail(c, DWF_EINVAL,
                 "the gauge field of this precision is not built yet (dwf_load_gauge builds FP64 and FP32; "
                 "one dwf_apply_eo_dev call in a 16-bit precision builds that form)");
-  if (c->device < 0 || c->device >= kMaxStaticDevices) return fail(c, DWF_EINVAL, "device ordinal too large");
 
-  // carve five fields, the partial sums and the ticket out of the static array
+  // carve five fields, the scalar block, the partial sums and the ticket out of the array
   const size_t n = (size_t)c->h * c->Ns;
   const size_t data_b = round256(n * site_bytes(prec));
   const size_t nrm_b = prec >= P_F16 ? round256(n * sizeof(float)) : 0;
   const long spb = std::min(hop_sites_per_block(prec, c->Ns), sites_per_block(prec, c->Ns));
   const size_t max_blocks = std::max<size_t>((size_t)((c->h + spb - 1) / spb), (size_t)c->sm_count * 8);
-  const size_t need = 5 * (data_b + nrm_b) + round256(max_blocks * sizeof(double)) + 256;
+  const size_t need = 5 * (data_b + nrm_b) + round256(sizeof(CGScalars)) + round256(max_blocks * sizeof(double)) +
+                      256;
   if (need > kStaticScratchBytes)
     return fail(c, DWF_EINVAL,
                 "lattice too large for the static scratch: needs " + std::to_string(need) + " bytes, the array holds " +
                     std::to_string(kStaticScratchBytes));
-  void *base = nullptr;
-  CK(static_scratch_address(c->device, &base));
-  unsigned char *cur = static_cast<unsigned char *>(base);
+  // set-up, once per context (so once per device it runs on, with that device current):
+  // in host code the array's name is only a host-side stand-in, so its device address is
+  // looked up here; the first call on a context should come before any stream capture
+  if (!c->static_scratch) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_dwf_static_scratch);
+    if (e != cudaSuccess) return fail(c, DWF_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    c->static_scratch = p;
+  }
+  unsigned char *cur = static_cast<unsigned char *>(c->static_scratch);
   Field f[5];
   for (auto &x : f) {
     x.v = cur;
@@ -1779,53 +1756,88 @@ extern "C" dwf_status dwf_apply_eo_dev_static(dwf_ctx *c, int op, int prec, int 
     x.nrm = nrm_b ? reinterpret_cast<float *>(cur) : nullptr;
     cur += nrm_b;
   }
+  CGScalars *sc = reinterpret_cast<CGScalars *>(cur);
+  cur += round256(sizeof(CGScalars));
   double *part = reinterpret_cast<double *>(cur);
   cur += round256(max_blocks * sizeof(double));
   unsigned *ticket = reinterpret_cast<unsigned *>(cur);
 
   cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
-  ReductionScratchSwap swap(c, part, ticket);
-  // the array keeps the previous call's contents: the ticket must start at zero
+  // the array keeps the previous call's contents: the scalars (error word included) and the
+  // ticket must start at zero
+  CK(cudaMemsetAsync(sc, 0, sizeof(CGScalars), st));
   CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
   CK(cudaMemsetAsync(d_out, 0, full, st));
   const Geom g = geom(c);
-  const int cls = DWF_KC_OTHER;
   Field &in = f[0], &out = f[1], &tA = f[2], &tB = f[3], &tC = f[4];
   const int inpar = op == DWF_OP_DEO ? 1 : op == DWF_OP_DOE ? 0 : parity;
   const int outpar = op == DWF_OP_DEO ? 0 : op == DWF_OP_DOE ? 1 : parity;
-  {
-    Timed t(c, st, cls);
-    CK(pack_any(prec, d_in, in, g, inpar, c->sm_count, st));
-  }
+  // the hop launches of this call, with the reduction scratch of the array
+  auto hop_s = [&](int outp, int epi, Field x, Field y, Field o, bool m5, bool trans, double coef) -> cudaError_t {
+    HopArgs a = hop_args(c, prec, outp);
+    a.in = x;
+    a.y = y;
+    a.out = o;
+    if (m5) set_m5(a, c, prec, trans);
+    a.coef = coef;
+    a.sc = sc;
+    a.partials = part;
+    a.ticket = ticket;
+    return hop_any(prec, epi, a, st);
+  };
+  auto smix_s = [&](int mode, Field x, Field o, int kind) -> cudaError_t {
+    SmixArgs a;
+    memset(&a, 0, sizeof(a));
+    a.in = x;
+    a.out = o;
+    a.K = dmat(c, prec, kind);
+    a.K2 = dmat(c, prec, MK_ID);
+    a.coef = 1.0;
+    a.h = c->h;
+    a.Ns = c->Ns;
+    a.sc = sc;
+    return smix_any(prec, mode, a, st);
+  };
+  // Eq. 11 on Schur parity sp: C v = v - M5 D M5 D v (u = -1/2 M5 H v, out = v + 1/2 M5 H u)
+  auto apply_c = [&](int sp, Field v, Field o, Field u) -> cudaError_t {
+    cudaError_t e = hop_s(1 - sp, E_M, v, Field{}, u, true, false, -0.5);
+    if (e == cudaSuccess) e = hop_s(sp, E_M_XPAY, u, v, o, true, false, 0.5);
+    return e;
+  };
+  // C^dag v = g5 (1 - D M5^T D M5^T) g5 v (w = M5^T g5 v, t = -1/2 M5^T H w, q = v + 1/2 g5 H t)
+  auto apply_cdag = [&](int sp, Field v, Field q, Field w, Field t) -> cudaError_t {
+    cudaError_t e = smix_s(S_G5, v, w, MK_M5T);
+    if (e == cudaSuccess) e = hop_s(1 - sp, E_M, w, Field{}, t, true, true, -0.5);
+    if (e == cudaSuccess) e = hop_s(sp, E_XPAY_G5, t, v, q, false, false, 0.5);
+    return e;
+  };
+  CK(pack_any(prec, d_in, in, g, inpar, c->sm_count, st));
   switch (op) {
     case DWF_OP_DEO:
-    case DWF_OP_DOE: {
-      HopArgs a = hop_args(c, prec, outpar);
-      a.in = in;
-      a.out = out;
-      a.coef = -0.5;
-      TRY(hop(c, st, prec, E_PLAIN, a, cls));
+    case DWF_OP_DOE:
+      CK(hop_s(outpar, E_PLAIN, in, Field{}, out, false, false, -0.5));
       break;
-    }
     case DWF_OP_M5:
     case DWF_OP_M5T:
-      TRY(smix(c, st, prec, S_PLAIN, in, out, op == DWF_OP_M5 ? MK_M5 : MK_M5T, 1.0, cls));
+      CK(smix_s(S_PLAIN, in, out, op == DWF_OP_M5 ? MK_M5 : MK_M5T));
       break;
     case DWF_OP_C:
-      TRY(op_c(c, st, prec, parity, in, out, tA, cls));
+      CK(apply_c(parity, in, out, tA));
       break;
     case DWF_OP_CDAG:
-      TRY(op_cdag(c, st, prec, parity, in, out, tA, tB, cls));
+      CK(apply_cdag(parity, in, out, tA, tB));
       break;
     case DWF_OP_CCDAG:
-      TRY(op_cdag(c, st, prec, parity, in, tC, tA, tB, cls));
-      TRY(op_c(c, st, prec, parity, tC, out, tA, cls));
+      CK(apply_cdag(parity, in, tC, tA, tB));
+      CK(apply_c(parity, tC, out, tA));
       break;
   }
-  {
-    Timed t(c, st, cls);
-    CK(unpack_any(prec, out, d_out, g, outpar, c->sm_count, st));
-  }
+  CK(unpack_any(prec, out, d_out, g, outpar, c->sm_count, st));
+  // the call returns when its work is done: it waits for `stream` and reads the kernels'
+  // error word (a bounded device-side wait that gave up) into host memory of its own
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, &sc->error, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  return pull_scalars(c, st);
+  if (err) return fail(c, DWF_ETIMEOUT, "a device-side wait for the TMA link copy timed out");
+  return DWF_OK;
 }

@@ -63,6 +63,9 @@ struct dwf_ctx {
   // TMA copies, and whether the copies are left out so that the waits run out
   unsigned wait_tries = dwf::kWaitTries;
   int skip_copies = 0;
+  // device address of the allocation-free entry point's static array (looked up by the
+  // first dwf_apply_eo_dev_static call on this context)
+  void *static_scratch = nullptr;
   // profiling of the current call
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;

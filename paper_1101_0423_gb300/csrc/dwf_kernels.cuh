@@ -193,7 +193,7 @@ template <int EPI> struct EpiT {
 
 struct HopArgs {
   Field in, out, y, b, r;
-  const void *gauge;   // doubled gauge of the output parity: [cb][8][LREALS]
+  const void *gauge;   // doubled gauge of the output parity: [cb][SITE_LREALS], links [8][LREALS]
   const int *nbr;      // [cb][8] for the output parity
   const void *K;       // FP32 arithmetic: M5 or M5^T, dense, kernel order K[chi][t][s]
   const void *rec;     // FP64: the same as a recurrence table along s, per chirality Ns
@@ -245,7 +245,7 @@ template <int P> struct HopSmem {
   static constexpr bool F2 = !(P == P_F64);
   using RL = typename PT<P>::real;
   __host__ __device__ static size_t raw(int nsite) {
-    return (size_t)nsite * 8 * PT<P>::LREALS * sizeof(typename PT<P>::lreal);
+    return (size_t)nsite * PT<P>::SITE_LREALS * sizeof(typename PT<P>::lreal);
   }
   __host__ __device__ static size_t off_raw(int spb, int b) { return 64 + (size_t)b * align16(raw(spb)); }
   __host__ __device__ static size_t off_nbr(int spb, int nb, int b) {
@@ -261,17 +261,50 @@ template <int P> struct HopSmem {
   // FP32 links are used as copied; the 16-bit forms are expanded
   static constexpr bool EXPAND = F2 && P != P_F32;
   __host__ __device__ static size_t off_k(int spb, int Ns, int nb, bool has_m) {
-    const size_t e = off_exp(spb, nb) + (EXPAND ? (size_t)spb * 8 * 5 * 16 : 0);
+    const size_t e = off_exp(spb, nb) + (EXPAND ? (size_t)spb * LINK_SITE_F4 * 16 : 0);
     const size_t st = has_m ? 64 + stage(spb, Ns) : 0;
     return align16(e > st ? e : st);
   }
-  // M5 / M5^T: dense as (k, k) pairs (FP32 arithmetic) or a recurrence table of
-  // 2 chiralities x Ns steps x 8 reals (FP64)
+  // M5 / M5^T: dense (FP32 arithmetic) or a recurrence table of 2 chiralities x Ns steps x
+  // 8 reals (FP64).  Dense, even Ns: per chirality and t a row of Ns/2 pairs
+  // (K[b][t], K[b + Ns/2][t]), the second chirality kq_stride pairs after the first; odd Ns:
+  // (k, k) pairs K[chi][t][s].
+  __host__ __device__ static int kq_stride(int Ns) {
+    // pad so that the two chiralities' rows start 16 banks apart: a half-warp reads one t-row
+    // of each chirality at once (Ns/2 pairs = Ns words each, Ns <= 16), or one of a single
+    // chirality (Ns = 32)
+    return Ns * (Ns / 2) + ((16 - (Ns * Ns) % 32 + 32) % 32) / 2;
+  }
+  __host__ __device__ static size_t kbytes(int Ns) {
+    if (!F2) return (size_t)2 * Ns * 8 * sizeof(RL);
+    const size_t dense = (size_t)2 * Ns * Ns * 8, paired = (size_t)2 * kq_stride(Ns) * 8;
+    return dense > paired ? dense : paired;
+  }
   __host__ __device__ static size_t bytes(int spb, int Ns, int nb, bool has_m) {
-    return off_k(spb, Ns, nb, has_m) +
-           (has_m ? align16(F2 ? (size_t)2 * Ns * Ns * 8 : (size_t)2 * Ns * 8 * sizeof(RL)) : 0);
+    return off_k(spb, Ns, nb, has_m) + (has_m ? align16(kbytes(Ns)) : 0);
   }
 };
+
+// the dense FP32 M5 epilogue's layout with four K entries per 16-byte read (Ns divides 32)
+__host__ __device__ constexpr bool m5_quad(int Ns) { return Ns == 8 || Ns == 16 || Ns == 32; }
+
+// thread -> (site of the tile, s-slice) in the hop phase.  FP32-arithmetic kernels with Ns a
+// multiple of 8 give each quarter-warp eight consecutive slices of one site, so a warp holds
+// four sites.  An LDS.128 costs one wavefront per half-warp even when every lane reads the
+// same address (measured on GB300), so the broadcast link reads are shared by four sites per
+// two wavefronts instead of two; each site's gathers stay whole 128-byte lines (eight
+// slices x 16 bytes).  Otherwise thread = s + Ns * site, the Ns slices of a site adjacent.
+template <bool F2>
+__device__ __forceinline__ void hop_thread(int tid, int Ns, int spb, int &sl, int &s) {
+  if (F2 && (Ns & 7) == 0) {
+    const int g = tid >> 3;
+    sl = g % spb;
+    s = ((g / spb) << 3) | (tid & 7);
+  } else {
+    sl = tid / Ns;
+    s = tid - sl * Ns;
+  }
+}
 // kernels without an M5 epilogue run persistent CTAs (measured: hop_xpay 96 -> 79 us); the
 // M5 kernels keep one tile per CTA and the smaller footprint (a double-buffered persistent
 // form took hop_m5 93 -> 104 us and hop_update 158 -> 188 us by shrinking the L1)
@@ -299,9 +332,11 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
   constexpr bool F2 = SM::F2;
   extern __shared__ __align__(128) unsigned char sm[];
   const int Ns = NSC ? NSC : a.Ns;
-  const int s = threadIdx.x, sl = threadIdx.y, spb = blockDim.y;
+  const int spb = blockDim.y;
   const int tid = lin_tid();
   const int nthr = nthreads();
+  int sl, s;  // this thread's site of the tile and s-slice in the hop phase
+  hop_thread<F2>(tid, Ns, spb, sl, s);
   const long ntile = (a.h + spb - 1) / spb;
 
   if (a.use_flag && sc_->restart_flag) return;  // uniform over the grid
@@ -323,7 +358,7 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
     const int ns_t = (int)min((long)spb, a.h - c0);
     const uint32_t lbytes = (uint32_t)SM::raw(ns_t), nbytes = (uint32_t)ns_t * 8 * 4;
     mbar_expect_tx(bar + b, lbytes + nbytes);
-    bulk_g2s(sLb(b), static_cast<const typename T::lreal *>(a.gauge) + (size_t)c0 * 8 * T::LREALS, lbytes, bar + b);
+    bulk_g2s(sLb(b), static_cast<const typename T::lreal *>(a.gauge) + (size_t)c0 * T::SITE_LREALS, lbytes, bar + b);
     bulk_g2s(sNb(b), a.nbr + c0 * 8, nbytes, bar + b);
   };
   auto prefetch_ops = [&](long t) {
@@ -343,11 +378,32 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
   }
   if constexpr (E::has_m) {
     if constexpr (F2) {
-      const float *Kg = static_cast<const float *>(a.K);
+      const float *Kg = static_cast<const float *>(a.K);  // K[chi][t][s]
       float2 *sK2 = reinterpret_cast<float2 *>(sKb);
-      for (int i = tid; i < 2 * Ns * Ns; i += nthr) {
-        const float k = (float)a.coef * Kg[i];
-        sK2[i] = make_float2(k, k);
+      if (m5_quad(Ns)) {
+        // per chirality, t-pair and b: (K[b][t], K[b + Ns/2][t], K[b][t + 1], K[b + Ns/2][t + 1])
+        const int half = Ns >> 1;
+        float4 *sK4 = reinterpret_cast<float4 *>(sKb);
+        for (int i = tid; i < Ns * Ns / 2; i += nthr) {
+          const int chi = i / (half * half), rem = i - chi * half * half;
+          const int tp = rem / half, b = rem - tp * half;
+          const float *c0 = Kg + ((size_t)chi * Ns + 2 * tp) * Ns, *c1 = c0 + Ns;
+          const float cf = (float)a.coef;
+          sK4[i] = make_float4(cf * c0[b], cf * c0[b + half], cf * c1[b], cf * c1[b + half]);
+        }
+      } else if ((Ns & 1) == 0) {
+        const int half = Ns >> 1, kst = SM::kq_stride(Ns);
+        for (int i = tid; i < Ns * Ns; i += nthr) {
+          const int chi = i / (Ns * half), rem = i - chi * Ns * half;
+          const int t = rem / half, b = rem - t * half;
+          const float *col = Kg + ((size_t)chi * Ns + t) * Ns;
+          sK2[chi * kst + t * half + b] = make_float2((float)a.coef * col[b], (float)a.coef * col[b + half]);
+        }
+      } else {
+        for (int i = tid; i < 2 * Ns * Ns; i += nthr) {
+          const float k = (float)a.coef * Kg[i];
+          sK2[i] = make_float2(k, k);
+        }
       }
     } else {
       // the matrix acts on coef H: coef scales g and the closure (entries PS, PN, W)
@@ -409,14 +465,16 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
       for (int l = tid; l < nsite * 8; l += nthr) {
         float W[18];
         load_link<P>(sL + (size_t)l * T::LREALS, W);
+        float4 *o = sP + (size_t)(l >> 3) * LINK_SITE_F4 + (l & 7) * 5;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) sP[(size_t)l * 5 + e] = make_float4(W[4 * e], W[4 * e + 1], W[4 * e + 2], W[4 * e + 3]);
-        sP[(size_t)l * 5 + 4] = make_float4(W[16], W[17], 0.f, 0.f);
+        for (int e = 0; e < 4; ++e) o[e] = make_float4(W[4 * e], W[4 * e + 1], W[4 * e + 2], W[4 * e + 3]);
+        o[4] = make_float4(W[16], W[17], 0.f, 0.f);
       }
       __syncthreads();
     }
 
     R acc[24];
+    bool chunk_done = false;  // the M5 epilogue already stored this tile's results
     if (active) {
       const int *nb = sN + sl * 8;
       if constexpr (F2) {
@@ -425,7 +483,7 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
         for (int q = 0; q < 12; ++q) ac2[q] = pk2(0.f, 0.f);
         const SignPairs fw = sign_pairs(-1.f), bw = sign_pairs(1.f);
         const float4 *myW =
-            (SM::EXPAND ? sP : reinterpret_cast<const float4 *>(sL)) + (size_t)sl * 8 * 5;
+            (SM::EXPAND ? sP : reinterpret_cast<const float4 *>(sL)) + (size_t)sl * LINK_SITE_F4;
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
           float ps1[24];
@@ -449,7 +507,7 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
       } else {
 #pragma unroll
         for (int c = 0; c < 24; ++c) acc[c] = 0;
-        const typename T::lreal *myL = sL + (size_t)sl * 8 * T::LREALS;
+        const typename T::lreal *myL = sL + (size_t)sl * T::SITE_LREALS;
         R ps[24], W[18];
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
@@ -482,9 +540,142 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
       for (int c = 0; c < 24; ++c) mine[c] = acc[c];
       __syncthreads();
       if constexpr (F2) {
-        // FP32 arithmetic: dense, every (site, s) thread forms its own output row from the
-        // site's Ns staged rows (independent sums: latency is what limits these kernels)
-        if (active) {
+        if ((Ns & 1) == 0) {
+          // FP32 arithmetic, even Ns: thread = (site, chirality, slice pair (b, b + Ns/2)),
+          // forming 12 outputs (one chirality) of two slices from the site's staged rows:
+          // each row piece read serves two slices, and a half-warp reads the pieces of at
+          // most two (site, chirality) pairs (one shared-memory wavefront per half-warp)
+          const int half = Ns >> 1;
+          const bool quad = m5_quad(Ns);
+          int sl2, chi, bq;
+          if (quad) {
+            // Ns divides 32: each half-warp one chirality of 32/Ns sites (lanes chi, site, b),
+            // so the K entries a half-warp reads are one 16-byte row per b, for two t at once
+            const int lane = tid & 31, rest = lane & 15;
+            chi = lane >> 4;
+            bq = rest % half;
+            sl2 = (tid >> 5) * (32 / Ns) + rest / half;
+          } else {
+            sl2 = tid / Ns;
+            const int r2 = tid - sl2 * Ns;
+            chi = r2 >= half ? 1 : 0;
+            bq = r2 - chi * half;
+          }
+          const bool act2 = sl2 < nsite;
+          f2 o1[6], o2[6];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) o1[q] = o2[q] = pk2(0.f, 0.f);
+          // o1 += K[b][t] H_t, o2 += K[b + Ns/2][t] H_t on this chirality's 12 reals
+          auto step = [&](const R *row, float k1s, float k2s) {
+            const f2 k1 = pk2(k1s, k1s), k2 = pk2(k2s, k2s);
+            const float4 *v4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              const float4 v = v4[k];
+              const f2 lo = pk2(v.x, v.y), hi = pk2(v.z, v.w);
+              o1[2 * k] = fma2(k1, lo, o1[2 * k]);
+              o1[2 * k + 1] = fma2(k1, hi, o1[2 * k + 1]);
+              o2[2 * k] = fma2(k2, lo, o2[2 * k]);
+              o2[2 * k + 1] = fma2(k2, hi, o2[2 * k + 1]);
+            }
+          };
+          if (act2) {
+            const R *site = sB + (size_t)sl2 * sstride + 12 * chi;
+            if (quad) {
+              const float4 *kq = reinterpret_cast<const float4 *>(sKb) + chi * (half * half) + bq;
+#pragma unroll 2
+              for (int tp = 0; tp < half; ++tp) {
+                const float4 kk = kq[tp * half];
+                step(site + (2 * tp) * ROW, kk.x, kk.y);
+                step(site + (2 * tp + 1) * ROW, kk.z, kk.w);
+              }
+            } else {
+              const float2 *kq = reinterpret_cast<const float2 *>(sKb) + chi * SM::kq_stride(Ns) + bq;
+#pragma unroll 4
+              for (int t = 0; t < Ns; ++t) {
+                const float2 kk = kq[t * half];  // (K[b][t], K[b + Ns/2][t])
+                step(site + t * ROW, kk.x, kk.y);
+              }
+            }
+          }
+          if constexpr (!T::HALF) {
+            // FP32 storage: the epilogue works on this thread's six 16-byte chunks
+            // (chunks 3 chi .. 3 chi + 2 of slices b and b + Ns/2); for each chunk the
+            // threads of a (site, chirality) cover Ns/2 consecutive slices
+            chunk_done = true;
+            if (act2) {
+              const long cb2 = cb0 + sl2;
+              R alpha = 0;
+              if constexpr (EPI == E_CG_UPDATE) alpha = sc_->alpha_f;
+              auto emit = [&](int sv, const f2 (&o)[6]) {
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk) {
+                  const int k = 3 * chi + kk;
+                  R v[4];
+                  upk2(o[2 * kk], v[0], v[1]);
+                  upk2(o[2 * kk + 1], v[2], v[3]);
+                  if constexpr (EPI == E_M) {
+                    store_chunk<P>(F(a.out), cb2, sv, Ns, k, v);
+                  } else if constexpr (EPI == E_M_XPAY) {
+                    R y[4];
+                    load_chunk<P>(F(a.y), cb2, sv, Ns, k, y);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) v[j] += y[j];
+                    store_chunk<P>(F(a.out), cb2, sv, Ns, k, v);
+                  } else if constexpr (EPI == E_CG_UPDATE) {
+                    // Ap = y + K H; r -= alpha Ap (alpha formed with (p, A p))
+                    R y[4], r[4];
+                    load_chunk<P>(F(a.y), cb2, sv, Ns, k, y);
+                    load_chunk<P>(F(a.r), cb2, sv, Ns, k, r);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                      r[j] -= alpha * (y[j] + v[j]);
+                      part += r[j] * r[j];
+                    }
+                    store_chunk<P>(F(a.r), cb2, sv, Ns, k, r);
+                  } else if constexpr (EPI == E_RESID) {
+                    R y[4], bb[4];
+                    load_chunk<P>(F(a.y), cb2, sv, Ns, k, y);
+                    load_chunk<P>(F(a.b), cb2, sv, Ns, k, bb);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                      bb[j] -= y[j] + v[j];
+                      part += bb[j] * bb[j];
+                    }
+                    store_chunk<P>(F(a.out), cb2, sv, Ns, k, bb);
+                  }
+                }
+              };
+              emit(bq, o1);
+              emit(bq + half, o2);
+            }
+          } else {
+            // 16-bit storage normalises each (site, s) row as a whole: the results go back
+            // into the stage and the per-(site, s) epilogue below stores them
+            __syncthreads();  // every thread is done reading the staged rows
+            if (act2) {
+              float4 *w1 = reinterpret_cast<float4 *>(sB + (size_t)sl2 * sstride + (size_t)bq * ROW + 12 * chi);
+              float4 *w2 = reinterpret_cast<float4 *>(sB + (size_t)sl2 * sstride + (size_t)(bq + half) * ROW + 12 * chi);
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                float x0, x1, x2, x3;
+                upk2(o1[2 * k], x0, x1);
+                upk2(o1[2 * k + 1], x2, x3);
+                w1[k] = make_float4(x0, x1, x2, x3);
+                upk2(o2[2 * k], x0, x1);
+                upk2(o2[2 * k + 1], x2, x3);
+                w2[k] = make_float4(x0, x1, x2, x3);
+              }
+            }
+            __syncthreads();
+            if (active) {
+#pragma unroll
+              for (int c = 0; c < 24; ++c) acc[c] = mine[c];
+            }
+          }
+        } else if (active) {
+          // odd Ns: dense, every (site, s) thread forms its own output row from the site's
+          // Ns staged rows
           const R *site = sB + (size_t)sl * sstride;
           const f2 *sK2 = reinterpret_cast<const f2 *>(sKb);
           f2 o[12];
@@ -574,7 +765,7 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
         }
       }
     }
-    if (active) {
+    if (active && !chunk_done) {
       if constexpr (EPI == E_PLAIN) {
 #pragma unroll
         for (int c = 0; c < 24; ++c) acc[c] *= (R)a.coef;
@@ -921,8 +1112,10 @@ __global__ void k_gauge(const double *U, typename PT<P>::lreal *G, Geom g, int p
       dag = true;
     }
     const double *u = U + ((size_t)site * 4 + mu) * 18;
-    L *o = G + (size_t)i * LR;
+    L *o = G + (size_t)cb * PT<P>::SITE_LREALS + dir * LR;
     for (int e = 18; e < LR; ++e) o[e] = L(0.f);  // padding of the FP32 form
+    if (dir == 7)                                 // and of the site's block of links
+      for (int e = 8 * LR; e < PT<P>::SITE_LREALS; ++e) G[(size_t)cb * PT<P>::SITE_LREALS + e] = L(0.f);
     for (int a = 0; a < 3 && a * 6 < LR; ++a)
       for (int b = 0; b < 3; ++b) {
         double re = dag ? u[2 * (3 * b + a)] : u[2 * (3 * a + b)];

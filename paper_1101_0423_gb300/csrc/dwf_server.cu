@@ -58,7 +58,7 @@ size_t site_bytes(int prec) { return prec == DWF_PREC_F64 ? 192 : prec == DWF_PR
 size_t estimate_bytes(const int dims[4], int Ns, int prec, int system) {
   const size_t V4 = (size_t)dims[0] * dims[1] * dims[2] * dims[3], h = V4 / 2, n = h * Ns;
   size_t b = V4 * 72 * 8;                        // FP64 host-layout gauge copy
-  b += 2 * h * (1152 + 640);                     // doubled FP64 and FP32 gauges
+  b += 2 * h * (1152 + 656);                     // doubled FP64 and FP32 gauges
   if (prec >= DWF_PREC_F16) b += 2 * h * 192;    // doubled 16-bit gauge
   b += 2 * h * 32 + std::max<size_t>(h, 8192) * 8;
   b += (system == DWF_SYS_FULL ? 21 : 7) * n * 192;  // FP64 solver and reconstruction fields
