@@ -140,7 +140,8 @@ typedef struct {
     int converged;         /* 1 when true_res <= tol */
     double true_res;       /* |b - C C^dag x| / |b| in FP64 */
     double true_res_full;  /* |eta - D psi| / |eta| in FP64 (DWF_SYS_FULL only, else 0) */
-    double flops;          /* counted flops (fixed per-site counts, see the design notes) */
+    double flops;          /* counted flops: per 5D half-site, CG iteration 5472 + 192 Ns, FP64 restart
+                              5328 + 192 Ns, source preparation and reconstruction 5160 + 384 Ns */
     double time_ms;        /* device time of the whole call, CUDA events on its stream */
     double class_ms[DWF_KC_COUNT];   /* per kernel class, when profiling */
     int class_launches[DWF_KC_COUNT];
@@ -211,25 +212,33 @@ dwf_status dwf_propagator_dev(dwf_ctx *ctx, const int x0[4], const dwf_solve_par
                               dwf_solve_stats *stats, void *stream);
 
 /* Allocation-free variant of dwf_apply_eo_dev (the paper has no counterpart: it is a
- * service for callers that must not allocate device memory while they run -- code
- * recording a CUDA stream capture, where cudaMalloc is not allowed; applications whose
- * device memory is owned by their own pool allocator or held to a fixed budget; and
- * latency-critical paths where a first-call allocation would stall).
+ * service for callers that cannot let a library allocate device memory -- applications
+ * whose device memory is owned by their own pool allocator, such as a framework's caching
+ * allocator that already holds the GPU's memory, or held to a fixed budget decided at
+ * start-up -- and for paths that must not meet the device-wide synchronisation that a
+ * cudaMalloc or cudaFree can bring).
  * Applies DWF_OP_DEO, DOE, M5, M5T, C, CDAG or CCDAG exactly as dwf_apply_eo_dev does, with
- * the same arguments, but takes every work field and the reduction scratch from one static
- * device array of 64 MiB compiled into the library (held on every GPU that loads the
- * library until the process exits) and calls no cudaMalloc, cudaFree or other allocating
- * routine.  The caller still passes the input and output arrays.  Limits and behaviour:
+ * the same arguments, but takes every work field, the scalar block and the reduction
+ * scratch from one static device array of 64 MiB compiled into the library (held on every
+ * GPU that loads the library until the process exits) and calls no cudaMalloc, cudaFree or
+ * other allocating routine.  The caller still passes the input and output arrays.  Limits
+ * and behaviour:
  *   - five work fields plus the partial sums must fit in 64 MiB: about 5 * 24 * Ns * V4/2
  *     reals of the precision (FP32: Ns * V4/2 <= ~135,000; FP64: <= ~67,000, e.g. 8^4 x 16);
  *     larger lattices return DWF_EINVAL with the byte count in dwf_last_error;
  *   - the gauge field of `prec` must already exist (dwf_load_gauge builds FP64 and FP32; one
  *     dwf_apply_eo_dev call builds a 16-bit form), else DWF_EINVAL;
- *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *     with that device current; make that first call before any stream capture begins;
+ *   - set-up: the first call on a context looks up the array's device address
+ *     (cudaGetSymbolAddress) with the context's device current; that first call should
+ *     come before any stream capture;
+ *   - the call returns when its work is done: it synchronises `stream` and copies the
+ *     kernels' 4-byte error word to the host (DWF_ETIMEOUT if a bounded device-side wait
+ *     gave up);
  *   - every call shares the one array, which keeps the last call's contents; the call clears
  *     what must start at zero itself.  Calls that overlap on the GPU (two streams, two
- *     contexts, or two host threads) race on the array and must be serialised by the caller. */
+ *     contexts, or two host threads) race on the array and must be serialised by the
+ *     caller.  The context's own scratch is not used, so other calls on the context do not
+ *     touch the array. */
 dwf_status dwf_apply_eo_dev_static(dwf_ctx *ctx, int op, int prec, int parity, const double *d_in,
                                    double *d_out, void *stream);
 

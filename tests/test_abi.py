@@ -30,6 +30,50 @@ def declared_functions():
     return sorted(names)
 
 
+def declared_prototypes():
+    """{name: (return type, [parameter declarations])} of every function include/*.h declares."""
+    protos = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^\s*((?:const\s+)?[A-Za-z_]\w*\s*\**)\s*(dwf_\w+)\s*\(([^)]*)\)\s*;", text, flags=re.M):
+            params = [p.strip() for p in m.group(3).split(",") if p.strip() and p.strip() != "void"]
+            protos[m.group(2)] = (m.group(1).strip(), params)
+    return protos
+
+
+def _ctype_kind(t):
+    if t is None:
+        return "void"
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or t.__name__.startswith("LP_"):
+        return "ptr"
+    return {ctypes.c_int: "int", ctypes.c_uint: "unsigned", ctypes.c_double: "double",
+            ctypes.c_uint64: "uint64_t"}[t]
+
+
+def _c_kind(decl):
+    if "*" in decl or "[" in decl:
+        return "ptr"
+    words = decl.replace("const", " ").split()
+    base = words[0] if len(words) > 1 else words[0]
+    return {"dwf_status": "int", "int": "int", "unsigned": "unsigned", "double": "double",
+            "uint64_t": "uint64_t", "void": "void"}[base]
+
+
+def test_binding_prototypes_match_the_header(lib):
+    """Every ctypes prototype of the binding has the header's parameter count and kinds
+    (pointer / int / unsigned / double / uint64_t) and its return kind."""
+    protos = declared_prototypes()
+    assert "dwf_apply_eo_dev_static" in protos
+    assert set(protos) == set(declared_functions())
+    for name, (ret, params) in protos.items():
+        f = getattr(lib, name)
+        assert f.argtypes is not None, f"{name}: no ctypes prototype"
+        got = [_ctype_kind(t) for t in f.argtypes]
+        want = [_c_kind(p) for p in params]
+        assert got == want, f"{name}: binding {got} vs header {want}"
+        assert _ctype_kind(f.restype) == _c_kind(ret), f"{name}: return kind"
+
+
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ["dwf_create", "dwf_destroy", "dwf_load_gauge", "dwf_apply_eo", "dwf_solve"]:

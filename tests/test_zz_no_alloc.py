@@ -1,22 +1,25 @@
-"""The allocation-free operator entry point (dwf_apply_eo_dev_static) against dwf_apply_eo_dev.
+"""The allocation-free operator entry point (dwf_apply_eo_dev_static), against the FP64 CPU
+oracle and against dwf_apply_eo_dev.
 
-Some callers cannot allocate device memory while they run: a CUDA stream capture in
-progress forbids cudaMalloc, and applications that own all device memory through their
-own pool allocator (or a fixed budget) cannot let a library allocate behind their back.
-dwf_apply_eo_dev_static serves them from a static device array inside the library.  Both
-entry points are called through the C-ABI on the same inputs, twice in a row (the static
-array keeps the previous call's contents, so the second call checks that nothing stale
-leaks through), and must agree within the parity tests' tolerances: FP64 1e-12, FP32
-1e-5, fp16 5e-3 (relative to the largest component).  This file is collected last so a
+Some callers cannot let a library allocate device memory: applications whose GPU memory is
+owned by their own pool allocator (a framework's caching allocator already holding the
+device) or held to a fixed budget, and paths that must not meet the device-wide
+synchronisation a cudaMalloc/cudaFree can bring.  dwf_apply_eo_dev_static serves them
+from a static device array inside the library.  Every operator is called through the C-ABI
+on the same inputs, twice in a row (the static array keeps the previous call's contents,
+so the second call checks that nothing stale leaks through), and must agree with the
+oracle and with dwf_apply_eo_dev within the parity tests' tolerances: FP64 1e-12, FP32
+1e-5, fp16 5e-3 (max |difference| / max |reference|).  This file is collected last so a
 run that stops at the first failure has already run every other test.
 """
-import numpy as np
 import pytest
 
+import oracle
 from paper_1101_0423_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 TOL = {0: 1e-12, 1: 1e-5, 2: 5e-3}
+M0, MQ = 1.8, 0.03
 
 
 def _rel(a, b):
@@ -31,21 +34,40 @@ def setup():
     dims, ns = (6, 4, 4, 6), 12        # 288 half-lattice sites: several CTA tiles, ragged tail
     om, sg = inputs.weights("cosine", ns)
     U = inputs.gauge_field(dims, 0.5, seed=41)
-    ctx = dwf.Context(dims, ns, 1.8, 0.03, om, sg, U)
-    xs = [torch.from_numpy(inputs.gaussian_source(dims, ns, seed=42 + k)).cuda() for k in range(2)]
-    yield dwf, ctx, xs
+    ctx = dwf.Context(dims, ns, M0, MQ, om, sg, U)
+    xh = [inputs.gaussian_source(dims, ns, seed=42 + k) for k in range(2)]
+    xs = [torch.from_numpy(x).cuda() for x in xh]
+    mp, mm = oracle.m5(ns, M0, MQ, om, sg)
+    yield dwf, ctx, xs, dict(dims=dims, ns=ns, U=U, mp=mp, mm=mm, xh=xh)
     ctx.close()
+
+
+def _oracle(dwf, o, op, parity, x):
+    d, ns, U, mp, mm = o["dims"], o["ns"], o["U"], o["mp"], o["mm"]
+    if op == dwf.OP_DEO:
+        return oracle.hop(d, ns, U, 0, x)
+    if op == dwf.OP_DOE:
+        return oracle.hop(d, ns, U, 1, x)
+    if op == dwf.OP_M5:
+        return oracle.apply_s(d, ns, mp, mm, x, parity=parity)
+    if op == dwf.OP_M5T:
+        return oracle.apply_s(d, ns, mp, mm, x, transpose=True, parity=parity)
+    if op == dwf.OP_C:
+        return oracle.c_op(d, ns, U, mp, mm, parity, x)
+    if op == dwf.OP_CDAG:
+        return oracle.cdag_op(d, ns, U, mp, mm, parity, x)
+    return oracle.ccdag_op(d, ns, U, mp, mm, parity, x)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("opname", ["DEO", "DOE", "M5", "M5T", "C", "CDAG", "CCDAG"])
 @pytest.mark.parametrize("parity", [0, 1])
-def test_static_variant_matches_allocating_entry_point(setup, opname, prec, parity):
+def test_static_variant_matches_oracle_and_allocating_entry_point(setup, opname, prec, parity):
     import torch
-    dwf, ctx, xs = setup
+    dwf, ctx, xs, o = setup
     op = getattr(dwf, "OP_" + opname)
     stream = torch.cuda.current_stream()
-    for x in xs:                                   # two calls in a row
+    for x, xh in zip(xs, o["xh"]):                 # two calls in a row
         want = torch.empty_like(x)
         got = torch.full_like(x, float("nan"))     # the output is fully written by the call
         dwf.dwf_apply_eo_dev(ctx.h, op, prec, parity, x, want, stream=stream)
@@ -53,11 +75,13 @@ def test_static_variant_matches_allocating_entry_point(setup, opname, prec, pari
         stream.synchronize()
         assert not torch.isnan(got).any()
         assert _rel(got, want) <= TOL[prec]
+        ref = torch.from_numpy(_oracle(dwf, o, op, parity, xh))
+        assert _rel(got.cpu(), ref) <= TOL[prec]
 
 
 def test_static_variant_16bit_after_its_gauge_exists(setup):
     import torch
-    dwf, ctx, xs = setup
+    dwf, ctx, xs, o = setup
     stream = torch.cuda.current_stream()
     for x in xs:
         want, got = torch.empty_like(x), torch.empty_like(x)
@@ -69,7 +93,7 @@ def test_static_variant_16bit_after_its_gauge_exists(setup):
 
 def test_static_variant_rejects_what_it_cannot_serve(setup):
     import torch
-    dwf, ctx, xs = setup
+    dwf, ctx, xs, o = setup
     out = torch.empty_like(xs[0])
     with pytest.raises(dwf.DwfError) as e:
         dwf.dwf_apply_eo_dev_static(ctx.h, dwf.OP_DFULL, dwf.PREC_F32, 0, xs[0], out)
