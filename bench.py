@@ -301,15 +301,14 @@ def serve_measure(n, lattices, inner_prec, fractions, progress=False):
         est = sum(n / (f * capacity) for f in fractions)
         print(f"serve: capacity {capacity:.3f} solves/s; the {len(fractions)} arrival-rate runs take about "
               f"{est / 60:.0f} min", file=sys.stderr, flush=True)
-    out = []
     for f in fractions:
         if progress:
             print(f"serve: lambda = {f} x capacity ({n} requests)", file=sys.stderr, flush=True)
         st = serve_run(reqs, f * capacity, gauges_np, inner_prec)
-        out.append({"lambda_fraction": f, "lambda_per_s": f * capacity, "capacity_per_s": capacity,
-                    "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                    "mean_ms": st["mean_ms"], "completed": st["completed"], "ok": st["ok"]})
-    return out
+        yield {"lambda_fraction": f, "lambda_per_s": f * capacity, "capacity_per_s": capacity,
+               "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+               "mean_ms": st["mean_ms"], "completed": st["completed"], "ok": st["ok"],
+               "batched": st["batched"]}
 
 
 def odwf_measure(repeats=3):
@@ -416,6 +415,96 @@ def batch_measure():
     return out
 
 
+def _oracle_residual_worker(args):
+    """|eta - D psi| / |eta| by the FP64 oracle, one solution (spawned process)."""
+    import numpy as np
+    import oracle
+    from paper_1101_0423_gb300 import inputs
+    dims, ns, eps, gseed, mq, kind, eta, psi = args
+    om, sg = inputs.weights(kind, ns)
+    U = inputs.gauge_field(dims, eps, seed=gseed)
+    return float(np.linalg.norm(eta - oracle.dfull(dims, ns, U, M0, mq, om, sg, psi)) / np.linalg.norm(eta))
+
+
+def configs_measure():
+    """Every workload configuration solved on the GPU at its real size, its true residual
+    recomputed by the FP64 oracle on the host cores (a spawned pool, one solution per core):
+    4^4x8 Shamir normal equations; 16^3x32x16 cosine and Borici; the cosine solve with FP32,
+    bf16 and fp16 inner iterations; the 12 point sources on 24^3x48x16 as one batch; the
+    ragged set of 8 right-hand sides (Ns 8..32, masses 0.005..0.1) on 16^3x32."""
+    import multiprocessing as mp_
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1101_0423_gb300 import dwf, inputs
+    oracle.build()
+    pool = mp_.get_context("spawn").Pool(min(12, host_cores()))
+    rows, jobs = [], []
+    stream = torch.cuda.current_stream()
+
+    def solve(dims, ns, kind, mq, eps, gseed, eta, **kw):
+        om, sg = inputs.weights(kind, ns)
+        with dwf.Context(dims, ns, M0, mq, om, sg, inputs.gauge_field(dims, eps, seed=gseed)) as ctx:
+            d_eta = torch.from_numpy(eta).cuda()
+            d_psi = torch.empty_like(d_eta)
+            st = dwf.dwf_solve_dev(ctx.h, d_eta, d_psi, stream=stream, **kw)
+            return d_psi.cpu().numpy(), st
+
+    # 4^4 x 8 normal equations (the small workload): the oracle's C C^dag residual inline
+    d0, ns0 = (4, 4, 4, 4), 8
+    om0, sg0 = inputs.weights("shamir", ns0)
+    U0 = inputs.gauge_field(d0, 0.3, seed=1)
+    b0 = inputs.gaussian_source(d0, ns0, seed=1, parity=0)
+    x0, st0 = solve(d0, ns0, "shamir", 0.05, 0.3, 1, b0, system=dwf.SYS_NORMAL, schur_parity=0)
+    mp, mm = oracle.m5(ns0, M0, 0.05, om0, sg0)
+    r0 = np.linalg.norm(b0 - oracle.ccdag_op(d0, ns0, U0, mp, mm, 0, x0)) / np.linalg.norm(b0)
+    rows.append({"config": "4^4x8 Shamir mq 0.05, normal equations on even sites", "inner": "f32",
+                 "iters": st0["iters"], "restarts": st0["restarts"], "solve_ms": st0["time_ms"],
+                 "true_res_library": st0["true_res"], "true_res_oracle": float(r0)})
+    eta16 = inputs.gaussian_source(DIMS, NS, seed=SEED)
+    sols = {}
+    for kind, inner in (("cosine", "f32"), ("cosine", "bf16"), ("cosine", "f16"), ("borici", "f32")):
+        prec = {"f32": dwf.PREC_F32, "bf16": dwf.PREC_BF16, "f16": dwf.PREC_F16}[inner]
+        psi, st = solve(DIMS, NS, kind, MQ, EPS, SEED, eta16, inner_prec=prec)
+        if kind == "cosine":
+            sols[inner] = psi
+        rows.append({"config": f"16^3x32x16 {kind} mq 0.02", "inner": inner, "iters": st["iters"],
+                     "restarts": st["restarts"], "solve_ms": st["time_ms"], "true_res_library": st["true_res_full"]})
+        jobs.append((len(rows) - 1, (DIMS, NS, EPS, SEED, MQ, kind, eta16, psi)))
+    for inner in ("bf16", "f16"):
+        rows[[r["inner"] for r in rows].index(inner)]["rel_diff_vs_f32"] = float(
+            np.linalg.norm(sols[inner] - sols["f32"]) / np.linalg.norm(sols["f32"]))
+    # 12 point sources, 24^3 x 48 x 16 Shamir, one batch
+    d3 = (24, 24, 24, 48)
+    om3, sg3 = inputs.weights("shamir", NS)
+    src = np.stack([inputs.point_source(d3, NS, spin, col) for spin in range(4) for col in range(3)])
+    with dwf.Context(d3, NS, M0, 0.01, om3, sg3, inputs.gauge_field(d3, EPS, seed=3)) as ctx:
+        d_rhs = torch.from_numpy(src).cuda()
+        d_sol = torch.empty_like(d_rhs)
+        st3 = dwf.dwf_solve_batch_dev(ctx.h, 12, d_rhs, d_sol, stream=stream)
+        sol3 = d_sol.cpu().numpy()
+    for k in range(12):
+        rows.append({"config": f"24^3x48x16 Shamir mq 0.01, point source {k} (spin {k // 3}, colour {k % 3}), "
+                               "batch of 12", "inner": "f32", "iters": st3[k]["iters"],
+                     "restarts": st3[k]["restarts"], "solve_ms": st3[k]["time_ms"],
+                     "true_res_library": st3[k]["true_res_full"]})
+        jobs.append((len(rows) - 1, (d3, NS, EPS, 3, 0.01, "shamir", src[k], sol3[k])))
+    del d_rhs, d_sol
+    # the ragged set: 8 operators on 16^3 x 32
+    for i, (n, m) in enumerate(zip([8, 12, 16, 20, 24, 32, 12, 16], np.geomspace(0.005, 0.1, 8))):
+        eta = inputs.gaussian_source(DIMS, n, seed=200 + i)
+        psi, st = solve(DIMS, n, "shamir", float(m), EPS, 4, eta)
+        rows.append({"config": f"16^3x32 Shamir, ragged set member {i}: Ns {n}, mq {m:.4f}", "inner": "f32",
+                     "iters": st["iters"], "restarts": st["restarts"], "solve_ms": st["time_ms"],
+                     "true_res_library": st["true_res_full"]})
+        jobs.append((len(rows) - 1, (DIMS, n, EPS, 4, float(m), "shamir", eta, psi)))
+    for (i, _), res in zip(jobs, pool.imap(_oracle_residual_worker, [j for _, j in jobs])):
+        rows[i]["true_res_oracle"] = res
+    pool.close()
+    pool.join()
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -433,6 +522,9 @@ def main():
                     help="requests per arrival-rate run of --serve (the sweep lasts about 12.5 x this / capacity)")
     ap.add_argument("--odwf", action="store_true",
                     help="only the optimal-weights solve on 16^3x32x16 against the cosine weights")
+    ap.add_argument("--configs", action="store_true",
+                    help="only the per-configuration table: every workload at its real size, iterations, "
+                         "restarts and the oracle-recomputed true residual")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -441,6 +533,12 @@ def main():
         _b.build()
         for row in batch_measure():
             print(json.dumps(row))
+        return
+    if args.configs:
+        from paper_1101_0423_gb300 import build as _b
+        _b.build()
+        for row in configs_measure():
+            print(json.dumps(row), flush=True)
         return
     if args.odwf:
         from paper_1101_0423_gb300 import build as _b
@@ -454,8 +552,8 @@ def main():
                                  [0.2, 0.4, 0.6, 0.8, 0.95], progress=True):
             print(json.dumps({"metric": "served solves/s, p99 latency", "config": {
                 "workload": "served: uniform lattice {8^4,12^3x24,16^3x32,24^3x48} x Ns {8,16,24,32} x "
-                            "mq U[0.005,0.1] x {shamir,borici,cosine}, bf16 inner, tol 1e-10, 150 GB budget"},
-                **row}))
+                            "mq U[0.005,0.1] x {shamir,borici,cosine}, bf16 inner, tol 1e-10, 150 GB budget",
+                "requests": args.serve_requests}, **row}), flush=True)
         return
 
     import numpy as np
@@ -591,7 +689,7 @@ def main():
     if world == 1 and not args.no_serve:
         # bounded served sample: 12 Poisson-arriving requests at 0.8 of the measured capacity,
         # lattices up to 16^3x32 (the full sweep over all four lattices is `bench.py --serve`)
-        row = serve_measure(12, SERVE_LATTICES_FULL[:3], dwf.PREC_BF16, [0.8])[0]
+        row = next(serve_measure(12, SERVE_LATTICES_FULL[:3], dwf.PREC_BF16, [0.8]))
         out["served"] = {"solves_per_s": row["solves_per_s"], "p50_ms": row["p50_ms"], "p99_ms": row["p99_ms"],
                          "lambda_per_s": row["lambda_per_s"], "capacity_per_s": row["capacity_per_s"],
                          "requests": row["completed"], "ok": row["ok"],

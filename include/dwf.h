@@ -119,7 +119,12 @@ typedef struct {
                           Normal system: x0's sites of the other parity are ignored.
                           A source or guess with a non-finite entry gives DWF_EINVAL.
                           Right-hand sides of a batch are then solved one after another */
-    int reserved[3];
+    int no_autotune;   /* 0 (default): the first solve of a (device, inner precision, Ns,
+                          volume class) times the candidate launch shapes of the inner hop
+                          kernels on its own fields and keeps the fastest for the process
+                          (results agree with other shapes to rounding: only the order of
+                          the reductions' block sums differs); 1: the default shapes */
+    int reserved[2];
 } dwf_solve_params;
 
 /* kernel classes timed when params.profile != 0 */
@@ -171,6 +176,23 @@ dwf_status dwf_load_gauge(dwf_ctx *ctx, const double *U);
 /* Same from a device array (caller-owned, host gauge layout), ordered on `stream`
  * (a cudaStream_t; NULL = the context's stream). */
 dwf_status dwf_load_gauge_dev(dwf_ctx *ctx, const double *d_U, void *stream);
+
+/* Gauge fields shared by handle.  dwf_gauge_create copies a gauge field (host gauge layout,
+ * 72 * V4 doubles; dwf_gauge_create_dev: a caller-owned device array, read after the work
+ * already queued on `stream`) to the CUDA device current at the call; the object keeps that
+ * FP64 copy and builds the doubled per-parity link forms of each precision once, on the
+ * first use by any context.  dwf_attach_gauge makes a context of the same lattice use it
+ * instead of a private copy (its previous gauge, private or shared, is released); any
+ * number of contexts -- different Ns, masses and weights -- can share one gauge object.
+ * dwf_gauge_release drops the caller's reference; the object is freed when no context uses
+ * it any more.  A later dwf_load_gauge on a context detaches it again.  Links must be SU(3)
+ * for the 12-real 16-bit forms.  Errors: DWF_EINVAL (odd extent, lattice or device of the
+ * context and the gauge differ), DWF_ENOMEM, DWF_ECUDA. */
+typedef struct dwf_gauge dwf_gauge;
+dwf_status dwf_gauge_create(const int dims[4], const double *U, dwf_gauge **out);
+dwf_status dwf_gauge_create_dev(const int dims[4], const double *d_U, void *stream, dwf_gauge **out);
+dwf_status dwf_gauge_release(dwf_gauge *gauge);
+dwf_status dwf_attach_gauge(dwf_ctx *ctx, dwf_gauge *gauge);
 
 /* Apply operator `op` (DWF_OP_*) in precision `prec` (DWF_PREC_*) to a full-lattice host
  * array `in` (24*Ns*V4 doubles, host layout) and write the full-lattice host array
@@ -242,6 +264,14 @@ dwf_status dwf_propagator_dev(dwf_ctx *ctx, const int x0[4], const dwf_solve_par
 dwf_status dwf_apply_eo_dev_static(dwf_ctx *ctx, int op, int prec, int parity, const double *d_in,
                                    double *d_out, void *stream);
 
+/* The launch shape the autotuner chose for inner-CG kernel class `kclass` (DWF_KC_HOP_M5,
+ * DWF_KC_HOP_XPAY or DWF_KC_HOP_UPDATE) at precision `prec` (FP32, F16, BF16) for this
+ * context's Ns and volume on its device: *threads per CTA and *persistent (1: a grid of the
+ * CTAs resident at once walking all tiles; 0: one tile per CTA).  DWF_OK when tuned,
+ * DWF_EAGAIN (default shape filled in) when no solve has tuned it yet, DWF_EINVAL for other
+ * classes or precisions. */
+dwf_status dwf_tuned_shape(dwf_ctx *ctx, int prec, int kclass, int *threads, int *persistent);
+
 /* Solve.  DWF_SYS_FULL: rhs = eta, sol = psi (full-lattice host arrays) with D psi = eta.
  * DWF_SYS_NORMAL: rhs = b, sol = x on the sites of params->schur_parity with
  * C C^dag x = b (other sites of sol are set to 0).  params may be NULL (defaults);
@@ -257,12 +287,17 @@ dwf_status dwf_solve_dev(dwf_ctx *ctx, const double *d_rhs, double *d_sol,
 /* ---------------------------------------------------------------------------------------
  * Serving: a request loop over many solves (not in the paper, which runs one solve at a
  * time; it is the production form of the same Schur-complement CG).  The server keeps
- * gauge ensembles resident on the device, queues requests first come first served,
- * admits a request when a slot is free and its device-memory estimate fits the budget,
- * and runs admitted solves concurrently, each on its own CUDA stream, so work of requests
- * that arrive while others run overlaps on the GPU.  Every solve is deterministic (fixed
- * reduction order), so its result does not depend on what else runs beside it.
- * Uses the CUDA device current when dwf_server_create is called.
+ * gauge ensembles resident on the device (one shared dwf_gauge per ensemble), queues
+ * requests first come first served, admits a request when a slot is free and its
+ * device-memory estimate fits the budget, and runs admitted solves concurrently, each on
+ * its own CUDA stream, so work of requests that arrive while others run overlaps on the
+ * GPU.  Queued requests of the same operator and solver settings as the admitted one join
+ * it as rows of one batched solve (up to max_batch; 16-bit AUTO-mode requests run alone).
+ * Contexts are cached per operator and released, least recently used first, only when a
+ * new one needs the memory; releasing one does not synchronise the device.  Every solve,
+ * and every row of a batch, is deterministic (fixed reduction order), so its result does
+ * not depend on what else runs beside it.  Uses the CUDA device current when
+ * dwf_server_create is called.
  * --------------------------------------------------------------------------------------- */
 typedef struct dwf_server dwf_server;
 
@@ -270,7 +305,8 @@ typedef struct {
     double hbm_budget_gb;   /* device memory the server may hold for contexts and solver
                                state, GiB (default 150) */
     int max_inflight;       /* solves running at once (default 4) */
-    int reserved[7];
+    int max_batch;          /* most requests of one operator run as one batch (0: 8) */
+    int reserved[6];
 } dwf_server_params;
 
 typedef struct {
@@ -298,6 +334,7 @@ typedef struct {
     double solves_per_s;             /* completed / (last completion - first submission) */
     double hbm_reserved_gb;          /* device-memory estimate of the admitted contexts */
     long long cancelled;             /* requests withdrawn by dwf_cancel before admission */
+    long long batched;               /* requests that ran as rows of a shared batch */
 } dwf_server_stats;
 
 void dwf_server_params_default(dwf_server_params *p);

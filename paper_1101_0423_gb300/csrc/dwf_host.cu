@@ -13,12 +13,85 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <string>
 #include <vector>
 
 #include "dwf_internal.h"
 
 using namespace dwf;
+
+// ------------------------------------------------------------------ memory
+
+namespace dwf {
+
+namespace {
+constexpr int kMaxPoolDevices = 256;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+std::mutex g_pinned_mu;
+std::multimap<size_t, void *> g_pinned_free;  // size class -> free pinned block
+size_t pinned_class(size_t bytes) { return (bytes + 4095) & ~(size_t)4095; }
+}  // namespace
+
+cudaError_t dmalloc(void **p, size_t bytes, int device, cudaStream_t st) {
+  *p = nullptr;
+  if (device < 0 || device >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pools[device]) {
+      cudaMemPoolProps props;
+      memset(&props, 0, sizeof(props));
+      props.allocType = cudaMemAllocationTypePinned;
+      props.handleTypes = cudaMemHandleTypeNone;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = device;
+      cudaMemPool_t np;
+      cudaError_t e = cudaMemPoolCreate(&np, &props);
+      if (e != cudaSuccess) return e;
+      // keep freed blocks in the pool (they serve the next context) instead of returning
+      // them to the driver at the next synchronisation
+      uint64_t keep = UINT64_MAX;
+      e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) {
+        cudaMemPoolDestroy(np);
+        return e;
+      }
+      g_pools[device] = np;
+    }
+    pool = g_pools[device];
+  }
+  return cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, st);
+}
+
+void dfree(void *p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+void *pinned_get(size_t bytes) {
+  const size_t cls = pinned_class(bytes);
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    auto it = g_pinned_free.find(cls);
+    if (it != g_pinned_free.end()) {
+      void *p = it->second;
+      g_pinned_free.erase(it);
+      return p;
+    }
+  }
+  void *p = nullptr;
+  if (cudaMallocHost(&p, cls) != cudaSuccess) return nullptr;
+  return p;
+}
+
+void pinned_put(void *p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(g_pinned_mu);
+  g_pinned_free.emplace(pinned_class(bytes), p);
+}
+
+}  // namespace dwf
 
 namespace {
 
@@ -258,9 +331,9 @@ dwf_status get_buf(dwf_ctx *c, const std::string &name, int prec, Field *f) {
   const std::string key = name + "#" + std::to_string(prec);
   Buf &b = c->bufs[key];
   if (!b.v) {
-    CK(cudaMalloc(&b.v, bytes));
+    CK(dmalloc(&b.v, bytes, c->device, c->stream));
     b.bytes = bytes;
-    if (prec >= P_F16) CK(cudaMalloc((void **)&b.nrm, n * sizeof(float)));
+    if (prec >= P_F16) CK(dmalloc((void **)&b.nrm, n * sizeof(float), c->device, c->stream));
     CK(cudaMemsetAsync(b.v, 0, bytes, c->stream));
     if (b.nrm) CK(cudaMemsetAsync(b.nrm, 0, n * sizeof(float), c->stream));
     CK(cudaStreamSynchronize(c->stream));  // ordered before any use on another stream
@@ -273,11 +346,12 @@ dwf_status get_buf(dwf_ctx *c, const std::string &name, int prec, Field *f) {
 dwf_status get_raw(dwf_ctx *c, const std::string &name, size_t bytes, void **p) {
   Buf &b = c->bufs["raw:" + name];
   if (b.v && b.bytes < bytes) {
-    cudaFree(b.v);
+    dfree(b.v, c->stream);
     b.v = nullptr;
   }
   if (!b.v) {
-    CK(cudaMalloc(&b.v, bytes));
+    CK(dmalloc(&b.v, bytes, c->device, c->stream));
+    CK(cudaStreamSynchronize(c->stream));  // ordered before any use on another stream
     b.bytes = bytes;
   }
   *p = b.v;
@@ -406,18 +480,39 @@ size_t link_bytes_per_site(int prec) {
   }
 }
 
-// doubled gauge field of precision prec, built on first use
+// doubled gauge field of precision prec, built on first use (in the shared gauge object
+// when the context is attached to one, once for all its contexts)
 dwf_status ensure_gauge(dwf_ctx *c, int prec, cudaStream_t st) {
   if (!c->gauge_loaded) return fail(c, DWF_ENOGAUGE, "dwf_load_gauge has not been called");
   if (c->gauge_ready[prec]) return DWF_OK;
+  if (dwf_gauge *G = c->shared) {
+    std::lock_guard<std::mutex> lock(G->mu);
+    if (!G->ready[prec]) {
+      for (int p = 0; p < 2; ++p) {
+        if (!G->d_gauge[prec][p])
+          CK(dmalloc(&G->d_gauge[prec][p], (size_t)G->h * link_bytes_per_site(prec), G->device, G->stream));
+        CK(gauge_any(prec, G->d_U, G->d_gauge[prec][p], geom(c), p, c->sm_count, G->stream));
+      }
+      CK(cudaStreamSynchronize(G->stream));  // complete before any context's stream uses it
+      G->ready[prec] = true;
+    }
+    for (int p = 0; p < 2; ++p) c->d_gauge[prec][p] = G->d_gauge[prec][p];
+    c->gauge_ready[prec] = true;
+    return DWF_OK;
+  }
   for (int p = 0; p < 2; ++p) {
-    if (!c->d_gauge[prec][p]) CK(cudaMalloc(&c->d_gauge[prec][p], (size_t)c->h * link_bytes_per_site(prec)));
+    if (!c->d_gauge[prec][p])
+      CK(dmalloc(&c->d_gauge[prec][p], (size_t)c->h * link_bytes_per_site(prec), c->device, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     Timed t(c, st, DWF_KC_OTHER);
     CK(gauge_any(prec, c->d_U, c->d_gauge[prec][p], geom(c), p, c->sm_count, st));
   }
   c->gauge_ready[prec] = true;
   return DWF_OK;
 }
+
+// drops the context's gauge: its private copies, or its reference to a shared gauge
+void release_gauge(dwf_ctx *c);
 
 HopArgs hop_args(dwf_ctx *c, int prec, int outpar) {
   HopArgs a;
@@ -435,7 +530,19 @@ HopArgs hop_args(dwf_ctx *c, int prec, int outpar) {
   return a;
 }
 
+// launch shapes picked by the autotuner, per (device, precision, epilogue, Ns, volume class)
+TuneCache g_tune;
+
+TuneCache::Key tune_key(const dwf_ctx *c, int prec, int epi) {
+  return TuneCache::Key(c->device, prec, epi, c->Ns, volume_class(c->h));
+}
+
 dwf_status hop(dwf_ctx *c, cudaStream_t st, int prec, int epi, HopArgs a, int cls) {
+  HopShape shape;
+  if (prec != P_F64 && c->use_tuned && g_tune.get(tune_key(c, prec, epi), &shape)) {
+    a.shape_threads = shape.threads;
+    a.shape_persistent = shape.persistent ? 1 : 0;
+  }
   Timed t(c, st, cls);
   CK(hop_any(prec, epi, a, st));
   return DWF_OK;
@@ -698,35 +805,42 @@ dwf_status dwf_create(const int dims[4], int Ns, double m0, double mq, const dou
           kd[(size_t)chi * Ns * Ns + (size_t)t * Ns + s] = v;
           kf[(size_t)chi * Ns * Ns + (size_t)t * Ns + s] = (float)v;
         }
-    if ((e = cudaMalloc(&c->dmat[0][k], nm * sizeof(double))) != cudaSuccess) return bail(e);
-    if ((e = cudaMalloc(&c->dmat[1][k], nm * sizeof(float))) != cudaSuccess) return bail(e);
-    if ((e = cudaMemcpy(c->dmat[0][k], kd.data(), nm * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = dmalloc(&c->dmat[0][k], nm * sizeof(double), c->device, c->stream)) != cudaSuccess) return bail(e);
+    if ((e = dmalloc(&c->dmat[1][k], nm * sizeof(float), c->device, c->stream)) != cudaSuccess) return bail(e);
+    if ((e = cudaMemcpyAsync(c->dmat[0][k], kd.data(), nm * sizeof(double), cudaMemcpyHostToDevice, c->stream)) !=
+        cudaSuccess)
       return bail(e);
-    if ((e = cudaMemcpy(c->dmat[1][k], kf.data(), nm * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(c->dmat[1][k], kf.data(), nm * sizeof(float), cudaMemcpyHostToDevice, c->stream)) !=
+        cudaSuccess)
       return bail(e);
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(e);  // kd, kf are reused
   }
   for (int tr = 0; tr < 2; ++tr) {
     const size_t nr = c->rec[tr].size();
     std::vector<float> rf(c->rec[tr].begin(), c->rec[tr].end());
-    if ((e = cudaMalloc(&c->drec[0][tr], nr * sizeof(double))) != cudaSuccess) return bail(e);
-    if ((e = cudaMalloc(&c->drec[1][tr], nr * sizeof(float))) != cudaSuccess) return bail(e);
-    if ((e = cudaMemcpy(c->drec[0][tr], c->rec[tr].data(), nr * sizeof(double), cudaMemcpyHostToDevice)) !=
+    if ((e = dmalloc(&c->drec[0][tr], nr * sizeof(double), c->device, c->stream)) != cudaSuccess) return bail(e);
+    if ((e = dmalloc(&c->drec[1][tr], nr * sizeof(float), c->device, c->stream)) != cudaSuccess) return bail(e);
+    if ((e = cudaMemcpyAsync(c->drec[0][tr], c->rec[tr].data(), nr * sizeof(double), cudaMemcpyHostToDevice,
+                             c->stream)) != cudaSuccess)
+      return bail(e);
+    if ((e = cudaMemcpyAsync(c->drec[1][tr], rf.data(), nr * sizeof(float), cudaMemcpyHostToDevice, c->stream)) !=
         cudaSuccess)
       return bail(e);
-    if ((e = cudaMemcpy(c->drec[1][tr], rf.data(), nr * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
-      return bail(e);
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(e);  // rf is a temporary
   }
   Geom g = geom(c);
   for (int p = 0; p < 2; ++p) {
-    if ((e = cudaMalloc((void **)&c->d_nbr[p], (size_t)c->h * 8 * sizeof(int))) != cudaSuccess) return bail(e);
+    if ((e = dmalloc((void **)&c->d_nbr[p], (size_t)c->h * 8 * sizeof(int), c->device, c->stream)) != cudaSuccess)
+      return bail(e);
     if ((e = neighbours_launch(c->d_nbr[p], g, p, c->sm_count, c->stream)) != cudaSuccess) return bail(e);
   }
-  if ((e = cudaMalloc((void **)&c->d_sc, sizeof(CGScalars))) != cudaSuccess) return bail(e);
-  if ((e = cudaMallocHost((void **)&c->h_sc, sizeof(CGScalars))) != cudaSuccess) return bail(e);
+  if ((e = dmalloc((void **)&c->d_sc, sizeof(CGScalars), c->device, c->stream)) != cudaSuccess) return bail(e);
+  if (!(c->h_sc = static_cast<CGScalars *>(pinned_get(sizeof(CGScalars))))) return bail(cudaErrorMemoryAllocation);
   memset(c->h_sc, 0, sizeof(CGScalars));
   c->part_len = std::max<size_t>((size_t)c->h, 8192);
-  if ((e = cudaMalloc((void **)&c->d_part, c->part_len * sizeof(double))) != cudaSuccess) return bail(e);
-  if ((e = cudaMalloc((void **)&c->d_ticket, sizeof(unsigned))) != cudaSuccess) return bail(e);
+  if ((e = dmalloc((void **)&c->d_part, c->part_len * sizeof(double), c->device, c->stream)) != cudaSuccess)
+    return bail(e);
+  if ((e = dmalloc((void **)&c->d_ticket, sizeof(unsigned), c->device, c->stream)) != cudaSuccess) return bail(e);
   if ((e = cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream)) != cudaSuccess) return bail(e);
   if ((e = cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(CGScalars), cudaMemcpyHostToDevice, c->stream)) !=
       cudaSuccess)
@@ -739,28 +853,28 @@ dwf_status dwf_create(const int dims[4], int Ns, double m0, double mq, const dou
 dwf_status dwf_destroy(dwf_ctx *c) {
   if (!c) return DWF_OK;
   cudaSetDevice(c->device);
-  if (c->stream) cudaStreamSynchronize(c->stream);
-  for (auto &kv : c->bufs) {
-    if (kv.second.v) cudaFree(kv.second.v);
-    if (kv.second.nrm) cudaFree(kv.second.nrm);
+  // every call on the context has finished its work (each waits for its stream), so the
+  // buffers go back to the pool in the context stream's order: nothing synchronises the
+  // device, and solves of other contexts keep running
+  if (c->stream) {
+    cudaStreamSynchronize(c->stream);
+    for (auto &kv : c->bufs) {
+      dfree(kv.second.v, c->stream);
+      dfree(kv.second.nrm, c->stream);
+    }
+    for (auto &row : c->dmat)
+      for (void *p : row) dfree(p, c->stream);
+    for (auto &row : c->drec)
+      for (void *p : row) dfree(p, c->stream);
+    release_gauge(c);
+    for (int *p : c->d_nbr) dfree(p, c->stream);
+    dfree(c->d_sc, c->stream);
+    dfree(c->d_part, c->stream);
+    dfree(c->d_ticket, c->stream);
+    cudaStreamSynchronize(c->stream);
   }
-  for (auto &row : c->dmat)
-    for (void *p : row)
-      if (p) cudaFree(p);
-  for (auto &row : c->drec)
-    for (void *p : row)
-      if (p) cudaFree(p);
-  for (auto &row : c->d_gauge)
-    for (void *p : row)
-      if (p) cudaFree(p);
-  for (int *p : c->d_nbr)
-    if (p) cudaFree(p);
-  if (c->d_U) cudaFree(c->d_U);
-  if (c->d_sc) cudaFree(c->d_sc);
-  if (c->h_sc) cudaFreeHost(c->h_sc);
-  if (c->h_scb) cudaFreeHost(c->h_scb);
-  if (c->d_part) cudaFree(c->d_part);
-  if (c->d_ticket) cudaFree(c->d_ticket);
+  pinned_put(c->h_sc, sizeof(CGScalars));
+  pinned_put(c->h_scb, c->h_scb_cap * sizeof(CGScalars));
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -772,7 +886,11 @@ dwf_status dwf_load_gauge_dev(dwf_ctx *c, const double *d_U, void *stream) {
   if (!d_U) return fail(c, DWF_EINVAL, "null gauge pointer");
   cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
   const size_t bytes = (size_t)c->V4 * 72 * sizeof(double);
-  if (!c->d_U) CK(cudaMalloc((void **)&c->d_U, bytes));
+  if (c->shared) release_gauge(c);  // back to a private copy
+  if (!c->d_U) {
+    CK(dmalloc((void **)&c->d_U, bytes, c->device, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
   CK(cudaMemcpyAsync(c->d_U, d_U, bytes, cudaMemcpyDeviceToDevice, st));
   c->gauge_loaded = true;
   for (int p = 0; p < 4; ++p) c->gauge_ready[p] = false;
@@ -787,13 +905,133 @@ dwf_status dwf_load_gauge(dwf_ctx *c, const double *U) {
   TRY(check_ctx(c));
   if (!U) return fail(c, DWF_EINVAL, "null gauge pointer");
   const size_t bytes = (size_t)c->V4 * 72 * sizeof(double);
-  if (!c->d_U) CK(cudaMalloc((void **)&c->d_U, bytes));
+  if (c->shared) release_gauge(c);  // back to a private copy
+  if (!c->d_U) CK(dmalloc((void **)&c->d_U, bytes, c->device, c->stream));
   CK(cudaMemcpyAsync(c->d_U, U, bytes, cudaMemcpyHostToDevice, c->stream));
   c->gauge_loaded = true;
   for (int p = 0; p < 4; ++p) c->gauge_ready[p] = false;
   TRY(ensure_gauge(c, P_F64, c->stream));
   TRY(ensure_gauge(c, P_F32, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  return DWF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+void gauge_unref(dwf_gauge *G) {
+  bool last;
+  {
+    std::lock_guard<std::mutex> lock(G->mu);
+    last = --G->refs == 0;
+  }
+  if (!last) return;
+  cudaSetDevice(G->device);
+  dfree(G->d_U, G->stream);
+  for (auto &row : G->d_gauge)
+    for (void *p : row) dfree(p, G->stream);
+  cudaStreamSynchronize(G->stream);
+  cudaStreamDestroy(G->stream);
+  delete G;
+}
+
+void release_gauge(dwf_ctx *c) {
+  if (c->shared) {
+    // the context's stream has finished its work with the shared arrays
+    gauge_unref(c->shared);
+    c->shared = nullptr;
+    c->d_U = nullptr;
+    for (auto &row : c->d_gauge)
+      for (auto &p : row) p = nullptr;
+  } else {
+    dfree(c->d_U, c->stream);
+    c->d_U = nullptr;
+    for (auto &row : c->d_gauge)
+      for (auto &p : row) {
+        dfree(p, c->stream);
+        p = nullptr;
+      }
+  }
+  c->gauge_loaded = false;
+  for (bool &r : c->gauge_ready) r = false;
+}
+
+dwf_status gauge_create_impl(const int dims[4], const double *U, bool on_device, void *stream, dwf_gauge **out) {
+  if (!dims || !U || !out) return DWF_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < 4; ++i)
+    if (dims[i] < 2 || (dims[i] & 1)) return DWF_EINVAL;
+  dwf_gauge *G = new dwf_gauge();
+  memcpy(G->dims, dims, sizeof(G->dims));
+  G->V4 = (long)dims[0] * dims[1] * dims[2] * dims[3];
+  G->h = G->V4 / 2;
+  const size_t bytes = (size_t)G->V4 * 72 * sizeof(double);
+  cudaError_t e = cudaGetDevice(&G->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&G->sm_count, cudaDevAttrMultiProcessorCount, G->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = dmalloc((void **)&G->d_U, bytes, G->device, G->stream);
+  if (e == cudaSuccess && on_device && stream) {
+    // the copy waits for the caller's stream, where d_U may still be being written
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+      e = cudaEventRecord(ev, (cudaStream_t)stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(G->stream, ev, 0);
+      cudaEventDestroy(ev);
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(G->d_U, U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, G->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(G->stream);
+  if (e != cudaSuccess) {
+    if (G->stream) {
+      dfree(G->d_U, G->stream);
+      cudaStreamSynchronize(G->stream);
+      cudaStreamDestroy(G->stream);
+    }
+    delete G;
+    return e == cudaErrorMemoryAllocation ? DWF_ENOMEM : DWF_ECUDA;
+  }
+  *out = G;
+  return DWF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dwf_status dwf_gauge_create(const int dims[4], const double *U, dwf_gauge **out) {
+  return gauge_create_impl(dims, U, false, nullptr, out);
+}
+
+dwf_status dwf_gauge_create_dev(const int dims[4], const double *d_U, void *stream, dwf_gauge **out) {
+  return gauge_create_impl(dims, d_U, true, stream, out);
+}
+
+dwf_status dwf_gauge_release(dwf_gauge *g) {
+  if (g) gauge_unref(g);
+  return DWF_OK;
+}
+
+dwf_status dwf_attach_gauge(dwf_ctx *c, dwf_gauge *g) {
+  TRY(check_ctx(c));
+  if (!g) return fail(c, DWF_EINVAL, "null gauge handle");
+  if (memcmp(g->dims, c->dims, sizeof(c->dims)) != 0) return fail(c, DWF_EINVAL, "gauge lattice differs from the context's");
+  if (g->device != c->device) return fail(c, DWF_EINVAL, "gauge field lives on another device");
+  if (c->shared == g) return DWF_OK;
+  CK(cudaStreamSynchronize(c->stream));
+  release_gauge(c);
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    ++g->refs;
+  }
+  c->shared = g;
+  c->d_U = g->d_U;
+  c->gauge_loaded = true;
+  // the FP64 and FP32 forms are always needed (restart operator, inner CG)
+  TRY(ensure_gauge(c, P_F64, c->stream));
+  TRY(ensure_gauge(c, P_F32, c->stream));
   return DWF_OK;
 }
 
@@ -926,15 +1164,15 @@ dwf_status get_buf_k(dwf_ctx *c, const std::string &name, int prec, int K, Field
   const size_t bytes = n * site_bytes(prec);
   Buf &b = c->bufs["batch:" + name + "#" + std::to_string(prec)];
   if (b.v && b.bytes < bytes) {
-    cudaFree(b.v);
-    if (b.nrm) cudaFree(b.nrm);
+    dfree(b.v, c->stream);
+    dfree(b.nrm, c->stream);
     b.v = nullptr;
     b.nrm = nullptr;
   }
   if (!b.v) {
-    CK(cudaMalloc(&b.v, bytes));
+    CK(dmalloc(&b.v, bytes, c->device, c->stream));
     b.bytes = bytes;
-    if (prec >= P_F16) CK(cudaMalloc((void **)&b.nrm, n * sizeof(float)));
+    if (prec >= P_F16) CK(dmalloc((void **)&b.nrm, n * sizeof(float), c->device, c->stream));
     CK(cudaMemsetAsync(b.v, 0, bytes, c->stream));
     if (b.nrm) CK(cudaMemsetAsync(b.nrm, 0, n * sizeof(float), c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -964,10 +1202,10 @@ dwf_status batch_slots(dwf_ctx *c, int K, Slots *sl) {
   TRY(get_raw(c, "batch_ticket", K * sizeof(unsigned), &p));
   sl->d_ticket = static_cast<unsigned *>(p);
   if (c->h_scb_cap < K) {
-    if (c->h_scb) cudaFreeHost(c->h_scb);
-    c->h_scb = nullptr;
-    CK(cudaMallocHost((void **)&c->h_scb, K * sizeof(CGScalars)));
-    c->h_scb_cap = K;
+    pinned_put(c->h_scb, c->h_scb_cap * sizeof(CGScalars));
+    c->h_scb = static_cast<CGScalars *>(pinned_get(K * sizeof(CGScalars)));
+    c->h_scb_cap = c->h_scb ? K : 0;
+    if (!c->h_scb) return fail(c, DWF_ENOMEM, "pinned host memory for the batch scalars");
   }
   sl->h_sc = c->h_scb;
   memset(sl->h_sc, 0, K * sizeof(CGScalars));
@@ -1071,6 +1309,61 @@ dwf_status cg_iteration(dwf_ctx *c, cudaStream_t st, const SolveState &S, const 
   return DWF_OK;
 }
 
+// The autotuner: for each of the inner CG's three hop kernels (hop + M5, hop + g5 xpay and
+// norm, hop + M5 + CG update and norm) not yet tuned for this device, precision, Ns and
+// volume class, time every candidate launch shape (dwf_tune.h) on this solve's own fields
+// -- before they hold any state: the source preparation and the arming of the scalars
+// overwrite everything these launches write -- and keep the fastest for the process.  Runs
+// outside any stream capture; a candidate that fails to launch is skipped.
+dwf_status tune_inner(dwf_ctx *c, cudaStream_t st, const SolveState &S) {
+  const int P = S.prec;
+  if (P == P_F64) return DWF_OK;
+  HopArgs m = hop_args(c, P, S.op);
+  m.in = S.w;
+  m.out = S.t;
+  set_m5(m, c, P, true);
+  m.coef = -0.5;
+  HopArgs x = hop_args(c, P, S.sp);
+  x.in = S.t;
+  x.y = S.p;
+  x.out = S.q;
+  x.coef = 0.5;
+  x.fin = FIN_NONE;
+  HopArgs u = hop_args(c, P, S.sp);
+  u.in = S.u;
+  u.y = S.q;
+  u.r = S.r;
+  set_m5(u, c, P, false);
+  u.coef = 0.5;
+  u.fin = FIN_NONE;
+  const std::pair<int, HopArgs *> classes[3] = {{E_M, &m}, {E_XPAY_G5, &x}, {E_CG_UPDATE, &u}};
+  cudaEvent_t e0 = next_event(c), e1 = next_event(c);
+  for (const auto &cl : classes) {
+    HopShape have;
+    if (g_tune.get(tune_key(c, P, cl.first), &have)) continue;
+    std::vector<std::pair<HopShape, double>> timed;
+    for (const HopShape &cand : hop_candidates(c->Ns)) {
+      HopArgs a = *cl.second;
+      a.shape_threads = cand.threads;
+      a.shape_persistent = cand.persistent ? 1 : 0;
+      if (hop_any(P, cl.first, a, st) != cudaSuccess) {  // warm-up; skip shapes that cannot launch
+        cudaGetLastError();
+        continue;
+      }
+      constexpr int REPS = 3;
+      CK(cudaEventRecord(e0, st));
+      for (int r = 0; r < REPS; ++r) CK(hop_any(P, cl.first, a, st));
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      timed.emplace_back(cand, ms / REPS);
+    }
+    g_tune.put(tune_key(c, P, cl.first), pick_fastest(timed, HopShape{}));
+  }
+  return DWF_OK;
+}
+
 // FP64 restart of right-hand side k (Algorithm 2), with the context pointed at its slot:
 // x_hat += x + alpha p (the last inner step, which the skipped p-update did not add), x = 0,
 // r_hat = b - C C^dag x_hat, |r_hat|^2 -> red, r = r_hat in the inner precision, |r|^2 -> red2
@@ -1133,6 +1426,7 @@ constexpr int RS_DONE = 6;  // restart flag of a right-hand side that is finishe
 // per right-hand-side bookkeeping of the host loop
 struct RhsState {
   double bnorm2 = 0, rhat2 = 0, prev_rhat2 = 0, rr_last = 0, res_full = 0;
+  double tol = 0;  // relative Schur residual this right-hand side is solved to
   int restarts = 0, iters = 0, mode = DWF_MODE_RELIABLE;
   bool done = false, converged = false;
   dwf_status status = DWF_OK;
@@ -1177,6 +1471,13 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
     return DWF_OK;
   };
   TRY(inner_bufs());
+  struct TunedScope {  // the solve's own choice, restored for the context's later calls
+    dwf_ctx *c;
+    bool prev;
+    ~TunedScope() { c->use_tuned = prev; }
+  } tuned_scope{c, c->use_tuned};
+  c->use_tuned = !prm.no_autotune;
+  if (!prm.no_autotune) TRY(tune_inner(c, st, S));
   Field eta[2], etap[2], phi[2], psi[2], dpsi[2];
   if (full)
     for (int p = 0; p < 2; ++p) {
@@ -1277,7 +1578,10 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
     R[k].mode = prm.mode == DWF_MODE_DEFECT ? DWF_MODE_DEFECT : DWF_MODE_RELIABLE;
     R[k].done = R[k].converged = R[k].bnorm2 == 0.0;
   }
-  for (int k = 0; k < K; ++k) TRY(arm(k, tol_schur, true, true, R[k].rr_last));
+  for (int k = 0; k < K; ++k) {
+    R[k].tol = tol_schur;
+    TRY(arm(k, tol_schur, true, true, R[k].rr_last));
+  }
 
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
@@ -1297,9 +1601,8 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
     return true;
   };
 
-  // ---- mixed-precision CG until every |b_k - A x_hat_k| <= tol_now |b_k| (FP64)
-  auto cg_loop = [&](double tol_now) -> dwf_status {
-    const double tol2 = tol_now * tol_now;
+  // ---- mixed-precision CG until every |b_k - A x_hat_k| <= R[k].tol |b_k| (FP64)
+  auto cg_loop = [&]() -> dwf_status {
     while (!all_done()) {
       // one batch of inner iterations (the device skips a right-hand side once its restart
       // is due or it is finished)
@@ -1343,10 +1646,11 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
           fprintf(stderr, "dwf: rhs %d restart %d iter %d reason %d |r_iter|/|b| %.3e |r_true|/|b| %.3e mode %s\n", k,
                   R[k].restarts, R[k].iters, reason, sqrt(c->h_sc->rr / R[k].bnorm2), sqrt(R[k].rhat2 / R[k].bnorm2),
                   R[k].mode == DWF_MODE_DEFECT ? "defect" : "reliable");
+        const double tol_now = R[k].tol;
         if (!std::isfinite(R[k].rhat2)) {
           R[k].done = true;
           R[k].status = fail(c, DWF_ENOCONV, "residual is not finite");
-        } else if (R[k].rhat2 <= tol2 * R[k].bnorm2) {
+        } else if (R[k].rhat2 <= tol_now * tol_now * R[k].bnorm2) {
           R[k].done = R[k].converged = true;
         } else if (R[k].iters >= prm.max_iter) {
           R[k].done = true;
@@ -1432,26 +1736,23 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
     return DWF_OK;
   };
 
-  dwf_status loop_st = cg_loop(tol_schur);
+  dwf_status loop_st = cg_loop();
   if (loop_st != DWF_OK && loop_st != DWF_ENOCONV) return loop_st;
   if (full) {
     for (int k = 0; k < K; ++k) TRY(reconstruct(k));
-    // a system whose full residual still misses the target continues from x_hat with the
-    // Schur tolerance tightened once (one common target for those of a batch; the others
+    // a system whose full residual still misses the target continues from x_hat with its
+    // Schur tolerance tightened once (each row of a batch as it would alone; the others
     // stay parked)
-    double tighter = tol_schur;
     std::vector<int> again;
     for (int k = 0; k < K; ++k)
-      if (R[k].converged && R[k].res_full > prm.tol) {
-        again.push_back(k);
-        tighter = std::min(tighter, tol_schur * std::min(0.1, 0.5 * prm.tol / R[k].res_full));
-      }
+      if (R[k].converged && R[k].res_full > prm.tol) again.push_back(k);
     if (!again.empty()) {
       for (int k : again) {
+        R[k].tol = tol_schur * std::min(0.1, 0.5 * prm.tol / R[k].res_full);
         R[k].done = R[k].converged = false;
-        TRY(arm(k, tighter, false, R[k].mode == DWF_MODE_DEFECT, R[k].rr_last));
+        TRY(arm(k, R[k].tol, false, R[k].mode == DWF_MODE_DEFECT, R[k].rr_last));
       }
-      loop_st = cg_loop(tighter);
+      loop_st = cg_loop();
       if (loop_st != DWF_OK && loop_st != DWF_ENOCONV) return loop_st;
       for (int k : again) TRY(reconstruct(k));
     }
@@ -1611,6 +1912,25 @@ extern "C" dwf_status dwf_solve_batch_dev(dwf_ctx *c, int nrhs, const double *d_
   cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
   if (prm.use_x0) return warm_solve(c, nrhs, d_rhs, d_sol, prm, stats, st);
   return solve_core(c, nrhs, d_rhs, d_sol, prm, stats, st);
+}
+
+extern "C" dwf_status dwf_tuned_shape(dwf_ctx *c, int prec, int kclass, int *threads, int *persistent) {
+  TRY(check_ctx(c));
+  if (!threads || !persistent) return fail(c, DWF_EINVAL, "null output");
+  if (prec != P_F32 && prec != P_F16 && prec != P_BF16) return fail(c, DWF_EINVAL, "inner precisions only");
+  int epi;
+  switch (kclass) {
+    case DWF_KC_HOP_M5: epi = E_M; break;
+    case DWF_KC_HOP_XPAY: epi = E_XPAY_G5; break;
+    case DWF_KC_HOP_UPDATE: epi = E_CG_UPDATE; break;
+    default: return fail(c, DWF_EINVAL, "kernel class must be hop_m5, hop_xpay or hop_update");
+  }
+  HopShape s;
+  const bool tuned = g_tune.get(tune_key(c, prec, epi), &s);
+  if (!tuned) s.persistent = epi == E_XPAY_G5;  // the default shapes
+  *threads = s.threads;
+  *persistent = s.persistent ? 1 : 0;
+  return tuned ? DWF_OK : DWF_EAGAIN;
 }
 
 extern "C" dwf_status dwf_solve_dev(dwf_ctx *c, const double *d_rhs, double *d_sol, const dwf_solve_params *pp,

@@ -4,11 +4,13 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "../../include/dwf.h"
 #include "dwf_launch.cuh"
+#include "dwf_tune.h"
 
 namespace dwf {
 
@@ -27,7 +29,34 @@ struct ProfRec {
   cudaEvent_t a, b;
 };
 
+// Device memory of contexts and shared gauge fields comes from one library-owned,
+// stream-ordered pool per device (cudaMallocFromPoolAsync / cudaFreeAsync on the owner's
+// stream): releasing it does not synchronise the device, so a context destroyed while
+// other solves run does not stall them, and freed blocks stay in the pool for the next
+// context.  Pinned host mirrors come from a process-wide free list and are never handed
+// back to the driver (cudaFreeHost synchronises).
+cudaError_t dmalloc(void **p, size_t bytes, int device, cudaStream_t st);
+void dfree(void *p, cudaStream_t st);
+void *pinned_get(size_t bytes);
+void pinned_put(void *p, size_t bytes);
+
 }  // namespace dwf
+
+// a device-resident gauge field shared by handle among the contexts of one lattice: the
+// FP64 host-layout copy and the doubled per-parity forms of each precision, built on first
+// use by whichever context needs them; freed with its last reference
+struct dwf_gauge {
+  int dims[4];
+  long V4 = 0, h = 0;
+  int device = 0;
+  int sm_count = 0;
+  double *d_U = nullptr;
+  void *d_gauge[4][2] = {};
+  bool ready[4] = {false, false, false, false};
+  cudaStream_t stream = nullptr;  // allocation and build stream
+  std::mutex mu;
+  int refs = 1;  // the creator's reference plus one per attached context
+};
 
 struct dwf_ctx {
   int dims[4];
@@ -45,6 +74,7 @@ struct dwf_ctx {
   int *d_nbr[2] = {nullptr, nullptr};
   double *d_U = nullptr;  // FP64 host-layout copy of the gauge field
   void *d_gauge[4][2] = {};
+  dwf_gauge *shared = nullptr;  // when attached: d_U and d_gauge point into it
   bool gauge_loaded = false;
   bool gauge_ready[4] = {false, false, false, false};
   std::map<std::string, dwf::Buf> bufs;
@@ -66,6 +96,9 @@ struct dwf_ctx {
   // device address of the allocation-free entry point's static array (looked up by the
   // first dwf_apply_eo_dev_static call on this context)
   void *static_scratch = nullptr;
+  // the launches of the current call take the autotuner's shapes (off for a solve with
+  // no_autotune, which keeps the default shapes)
+  bool use_tuned = true;
   // profiling of the current call
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;

@@ -216,6 +216,9 @@ struct HopArgs {
   int nrhs;
   size_t fstride, nstride;
   size_t part_stride;
+  // launch shape chosen by the host (autotuner); 0 threads: the default shape
+  int shape_threads;
+  int shape_persistent;
 };
 
 __device__ __forceinline__ Field field_rhs(Field f, int rb, size_t fstride, size_t nstride) {

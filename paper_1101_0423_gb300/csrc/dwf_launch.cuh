@@ -2,7 +2,11 @@
 // precision in k_f64.cu / k_f32.cu / k_half.cu so the three compile in parallel.
 #pragma once
 
+#include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "dwf_kernels.cuh"
 
@@ -36,36 +40,55 @@ inline int vec_grid(long n, int sm_count) {
 
 template <int P, int EPI, int NSC>
 cudaError_t hop_go(const HopArgs &a, cudaStream_t st) {
-  const int spb = hop_sites_per_block(P, a.Ns);
+  // the shape the host chose (autotuner), else 128-thread CTAs, persistent without M5
+  int spb = hop_sites_per_block(P, a.Ns);
+  bool persistent = hop_persistent<EPI>();
+  if (a.shape_threads > 0) {
+    spb = std::max(1, std::min(64, a.shape_threads / a.Ns));
+    persistent = a.shape_persistent != 0;
+  }
+  if (spb * a.Ns > 256) return cudaErrorInvalidConfiguration;
   const size_t smem = hop_smem_bytes<P, EPI>(spb, a.Ns);
-  static std::atomic<size_t> configured{0};  // launches may come from several host threads
-  if (smem > 48 * 1024 && configured.load() < smem) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_hop<P, EPI, NSC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured.store(smem);
+  if (smem > 48 * 1024) {  // launches may come from several host threads
+    static std::mutex cmu;
+    static size_t configured = 0;
+    std::lock_guard<std::mutex> lock(cmu);
+    if (configured < smem) {
+      cudaError_t e =
+          cudaFuncSetAttribute(k_hop<P, EPI, NSC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      configured = smem;
+    }
   }
   const int nrhs = a.nrhs > 1 ? a.nrhs : 1;
   const long ntile = (a.h + spb - 1) / spb;
   long nblk = ntile;  // one tile per CTA
-  if constexpr (hop_persistent<EPI>()) {
+  if (persistent) {
     // persistent grid: as many CTAs per right-hand side as are resident at once, each taking
     // an equal number of tiles (the rows of a batch follow one another through the GPU, and
     // a finished right-hand side's row returns at once)
     const int nthr = a.Ns * spb;
-    const unsigned long long key = ((unsigned long long)smem << 20) | (unsigned long long)nthr;
-    static std::atomic<unsigned long long> cached_key{0};
-    static std::atomic<long> cached_res{0};
-    long res = cached_key.load() == key ? cached_res.load() : 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    // resident CTAs per GPU for this kernel, CTA size and shared memory (cached)
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, size_t>, long> resident;
+    const auto key = std::make_tuple(dev, nthr, smem);
+    long res = 0;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      auto it = resident.find(key);
+      if (it != resident.end()) res = it->second;
+    }
     if (res <= 0) {
-      int dev = 0, sms = 0, per = 0;
-      cudaError_t e = cudaGetDevice(&dev);
-      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      int sms = 0, per = 0;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hop<P, EPI, NSC>, nthr, smem);
       if (e != cudaSuccess) return e;
       res = (long)std::max(per, 1) * sms;
-      cached_res.store(res);
-      cached_key.store(key);
+      std::lock_guard<std::mutex> lock(mu);
+      resident[key] = res;
     }
     const long per_cta = (ntile + res - 1) / res;
     nblk = (ntile + per_cta - 1) / per_cta;
@@ -109,11 +132,15 @@ template <int P, int MODE>
 cudaError_t smix_go(const SmixArgs &a, cudaStream_t st) {
   const int spb = sites_per_block(P, a.Ns);
   const size_t smem = smix_smem_bytes<P>(spb, a.Ns, MODE == S_DUAL);
-  static std::atomic<size_t> configured{0};
-  if (smem > 48 * 1024 && configured.load() < smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_smix<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured.store(smem);
+  if (smem > 48 * 1024) {
+    static std::mutex cmu;
+    static size_t configured = 0;
+    std::lock_guard<std::mutex> lock(cmu);
+    if (configured < smem) {
+      cudaError_t e = cudaFuncSetAttribute(k_smix<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      configured = smem;
+    }
   }
   const long nblk = (a.h + spb - 1) / spb;
   k_smix<P, MODE><<<dim3((unsigned)nblk, a.nrhs > 1 ? a.nrhs : 1), dim3(a.Ns, spb), smem, st>>>(a);

@@ -22,6 +22,7 @@ PREC_F64, PREC_F32, PREC_F16, PREC_BF16 = range(4)
 MODE_AUTO, MODE_RELIABLE, MODE_DEFECT = range(3)
 SYS_FULL, SYS_NORMAL = range(2)
 KC_NAMES = ["hop_m5", "hop_xpay", "hop_update", "smix_p", "f64", "other"]
+KC_HOP_M5, KC_HOP_XPAY, KC_HOP_UPDATE = range(3)
 STATUS = ["DWF_OK", "DWF_EINVAL", "DWF_ENOMEM", "DWF_ENOCONV", "DWF_EBUSY", "DWF_EAGAIN",
           "DWF_ETIMEOUT", "DWF_ECUDA", "DWF_ENOGAUGE"]
 DWF_OK, DWF_EINVAL, DWF_ENOMEM, DWF_ENOCONV, DWF_EBUSY, DWF_EAGAIN, DWF_ETIMEOUT, DWF_ECUDA, \
@@ -39,7 +40,8 @@ class SolveParams(ctypes.Structure):
                 ("inner_prec", ctypes.c_int), ("mode", ctypes.c_int), ("system", ctypes.c_int),
                 ("schur_parity", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("profile", ctypes.c_int), ("stall_iters", ctypes.c_int),
-                ("schur_target_pct", ctypes.c_int), ("use_x0", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("schur_target_pct", ctypes.c_int), ("use_x0", ctypes.c_int), ("no_autotune", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class SolveStats(ctypes.Structure):
@@ -60,7 +62,7 @@ class SolveStats(ctypes.Structure):
 
 class ServerParams(ctypes.Structure):
     _fields_ = [("hbm_budget_gb", ctypes.c_double), ("max_inflight", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("max_batch", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class Request(ctypes.Structure):
@@ -80,7 +82,7 @@ class ServerStats(ctypes.Structure):
                 ("in_flight", ctypes.c_longlong), ("queued", ctypes.c_longlong),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
                 ("solves_per_s", ctypes.c_double), ("hbm_reserved_gb", ctypes.c_double),
-                ("cancelled", ctypes.c_longlong)]
+                ("cancelled", ctypes.c_longlong), ("batched", ctypes.c_longlong)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -107,6 +109,10 @@ def load(build_if_missing: bool = True):
         "dwf_destroy": ([vp], i),
         "dwf_load_gauge": ([vp, dp], i),
         "dwf_load_gauge_dev": ([vp, vp, vp], i),
+        "dwf_gauge_create": ([ip, dp, ctypes.POINTER(vp)], i),
+        "dwf_gauge_create_dev": ([ip, vp, vp, ctypes.POINTER(vp)], i),
+        "dwf_gauge_release": ([vp], i),
+        "dwf_attach_gauge": ([vp, vp], i),
         "dwf_apply_eo": ([vp, i, i, i, dp, dp], i),
         "dwf_apply_eo_dev": ([vp, i, i, i, vp, vp, vp], i),
         "dwf_apply_eo_dev_static": ([vp, i, i, i, vp, vp, vp], i),
@@ -129,6 +135,7 @@ def load(build_if_missing: bool = True):
         "dwf_server_get_stats": ([vp, ctypes.POINTER(ServerStats)], i),
         "dwf_optimal_weights": ([i, d, d, dp, dp], i),
         "dwf_debug_set_wait": ([vp, ctypes.c_uint, i], i),
+        "dwf_tuned_shape": ([vp, i, i, ip, ip], i),
         "dwf_cancel": ([vp, ctypes.c_uint64], i),
         "dwf_server_set_admission": ([vp, i], i),
     }
@@ -212,6 +219,33 @@ def dwf_load_gauge(ctx, U):
 
 def dwf_load_gauge_dev(ctx, d_U, stream=None):
     _check(ctx, load().dwf_load_gauge_dev(ctx, _ptr(d_U), _stream(stream)))
+
+
+def dwf_gauge_create(dims, U):
+    """A device-resident gauge field shareable by handle among contexts of this lattice."""
+    U = _f64(U)
+    out = ctypes.c_void_p()
+    st = load().dwf_gauge_create((ctypes.c_int * 4)(*[int(v) for v in dims]), _dp(U), ctypes.byref(out))
+    if st != DWF_OK:
+        raise DwfError(st, "dwf_gauge_create rejected the lattice or could not allocate")
+    return out.value
+
+
+def dwf_gauge_create_dev(dims, d_U, stream=None):
+    out = ctypes.c_void_p()
+    st = load().dwf_gauge_create_dev((ctypes.c_int * 4)(*[int(v) for v in dims]), _ptr(d_U), _stream(stream),
+                                     ctypes.byref(out))
+    if st != DWF_OK:
+        raise DwfError(st, "dwf_gauge_create_dev rejected the lattice or could not allocate")
+    return out.value
+
+
+def dwf_gauge_release(gauge):
+    _check(None, load().dwf_gauge_release(gauge))
+
+
+def dwf_attach_gauge(ctx, gauge):
+    _check(ctx, load().dwf_attach_gauge(ctx, gauge))
 
 
 def dwf_apply_eo(ctx, op, prec, parity, x) -> np.ndarray:
@@ -302,6 +336,15 @@ def dwf_propagator(ctx, dims, x0, params=None, allow_noconv=False, **kw):
     return out.view(np.complex128).reshape(v4, 4, 3, 4, 3), [stats[k].as_dict() for k in range(12)]
 
 
+def dwf_tuned_shape(ctx, prec, kclass):
+    """(threads per CTA, persistent, tuned) of an inner-CG hop kernel class for this context."""
+    t, p = ctypes.c_int(0), ctypes.c_int(0)
+    st = load().dwf_tuned_shape(ctx, int(prec), int(kclass), ctypes.byref(t), ctypes.byref(p))
+    if st not in (DWF_OK, DWF_EAGAIN):
+        _check(ctx, st)
+    return t.value, bool(p.value), st == DWF_OK
+
+
 def dwf_last_error(ctx) -> str:
     return load().dwf_last_error(ctx).decode()
 
@@ -315,11 +358,14 @@ def dwf_debug_set_wait(ctx, wait_tries=0, skip_copies=False):
 class Context:
     """Owns a dwf_ctx; closes it on exit."""
 
-    def __init__(self, dims, Ns, m0, mq, omega, sigma, U=None):
+    def __init__(self, dims, Ns, m0, mq, omega, sigma, U=None, gauge=None):
+        """U: a host gauge field copied into the context; gauge: a dwf_gauge handle to share."""
         self.dims, self.Ns = tuple(dims), int(Ns)
         self.h = dwf_create(dims, Ns, m0, mq, omega, sigma)
         if U is not None:
             dwf_load_gauge(self.h, U)
+        elif gauge is not None:
+            dwf_attach_gauge(self.h, gauge)
 
     def close(self):
         if self.h:

@@ -110,6 +110,38 @@ def test_server_statistics(served):
     assert all(r[1]["latency_ms"] >= r[1]["queue_ms"] >= 0 for r in results)
 
 
+def test_requests_of_one_operator_share_a_batch(gpu_lib):
+    """Requests of the same operator and settings queued together run as rows of one batched
+    solve; every row's result is bit for bit the solve of that right-hand side alone."""
+    dwf = gpu_lib
+    srv = dwf.dwf_server_create(hbm_budget_gb=20.0, max_inflight=1)
+    try:
+        case = CASES[3]
+        dims, ns, kind, mq, system, sp, prec, gseed = case
+        g = {(dims, gseed): dwf.dwf_server_add_gauge(srv, dims, inputs.gauge_field(dims, 0.5, seed=gseed))}
+        dwf.dwf_server_set_admission(srv, False)   # queue them all before any is admitted
+        seeds = [300 + i for i in range(5)]
+        tickets = []
+        for seed in seeds:
+            om, sg = inputs.weights(kind, ns)
+            rhs = inputs.gaussian_source(dims, ns, seed=seed)
+            tickets.append(dwf.dwf_submit(srv, dims, ns, M0, mq, om, sg, g[(dims, gseed)], rhs,
+                                          system=system, schur_parity=sp, inner_prec=prec, tol=1e-10))
+        dwf.dwf_server_set_admission(srv, True)
+        out = []
+        for t in tickets:
+            buf = np.empty(int(np.prod(dims)) * ns * 24)
+            while dwf.dwf_poll(srv, t, buf) is None:
+                time.sleep(0.005)
+            out.append(buf)
+        assert dwf.dwf_server_get_stats(srv)["batched"] == len(seeds)
+        for seed, x in zip(seeds, out):
+            alone = solve_alone(dwf, case, seed)[0]
+            assert np.array_equal(x, alone)
+    finally:
+        dwf.dwf_server_destroy(srv)
+
+
 def test_tight_budget_serialises_without_changing_results(gpu_lib):
     """A budget that fits one small solve at a time: all finish, results unchanged."""
     dwf = gpu_lib
