@@ -344,7 +344,9 @@ def batch_measure():
     """12 spin-colour point sources on 24^3 x 48 x 16 Shamir (mq = 0.01): one batched solve
     against the same 12 solved one after another; and a ragged set of 8 right-hand sides on
     16^3 x 32 with Ns in {8,12,16,20,24,32,12,16} and masses 0.005..0.1 (different operators),
-    served concurrently against solved one after another.  FP32 inner, FP64 restarts, 1e-10."""
+    served concurrently against solved one after another; and 8 sources of one operator on
+    8^4 x 16 and 12^3 x 24 x 16, single FP32 solves against batches in FP32, fp16 and bf16.
+    FP64 restarts, 1e-10."""
     import numpy as np
     import torch
     from paper_1101_0423_gb300 import dwf, inputs
@@ -412,6 +414,35 @@ def batch_measure():
     out.append({"workload": "ragged 8 rhs, 16^3x32, Ns {8,12,16,20,24,32,12,16}, mq 0.005..0.1, fp32 inner",
                 "served_concurrently": {"solves_per_s": 8 / tc, "seconds": tc, "ok": ok},
                 "sequential": {"solves_per_s": 8 / ts, "seconds": ts, "ok": seq_ok}})
+    # small volumes, where one right-hand side leaves most of the GPU idle: 8 sources of one
+    # operator on 8^4 x 16 and 12^3 x 24 x 16 (cosine, mq 0.02), single FP32 solves one after
+    # another against batches in FP32, fp16 and bf16 inner precision (all to 1e-10)
+    for dims in ((8, 8, 8, 8), (12, 12, 12, 24)):
+        om, sg = inputs.weights("cosine", NS)
+        Us = inputs.gauge_field(dims, EPS, seed=5)
+        src = np.stack([inputs.gaussian_source(dims, NS, seed=400 + k) for k in range(8)])
+        row = {"workload": f"8 sources of one operator, {'x'.join(map(str, dims))}x16 cosine mq 0.02"}
+        with dwf.Context(dims, NS, M0, MQ, om, sg, Us) as ctx:
+            d_rhs = torch.from_numpy(src).cuda()
+            d_sol = torch.empty_like(d_rhs)
+            dwf.dwf_solve_dev(ctx.h, d_rhs[0], d_sol[0], stream=stream)   # warm-up (tunes shapes)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = [dwf.dwf_solve_dev(ctx.h, d_rhs[k], d_sol[k], stream=stream) for k in range(8)]
+            torch.cuda.synchronize()
+            ts = time.perf_counter() - t0
+            row["single_f32_sequential"] = {"solves_per_s": 8 / ts, "iters": st[0]["iters"],
+                                            "max_true_res_full": max(x["true_res_full"] for x in st)}
+            for name, prec in (("batch_f32", dwf.PREC_F32), ("batch_fp16", dwf.PREC_F16), ("batch_bf16", dwf.PREC_BF16)):
+                dwf.dwf_solve_batch_dev(ctx.h, 8, d_rhs, d_sol, stream=stream, inner_prec=prec)  # warm-up
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = dwf.dwf_solve_batch_dev(ctx.h, 8, d_rhs, d_sol, stream=stream, inner_prec=prec)
+                torch.cuda.synchronize()
+                tb = time.perf_counter() - t0
+                row[name] = {"solves_per_s": 8 / tb, "iters": max(x["iters"] for x in st),
+                             "max_true_res_full": max(x["true_res_full"] for x in st)}
+        out.append(row)
     return out
 
 
