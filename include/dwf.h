@@ -264,6 +264,33 @@ dwf_status dwf_propagator_dev(dwf_ctx *ctx, const int x0[4], const dwf_solve_par
 dwf_status dwf_apply_eo_dev_static(dwf_ctx *ctx, int op, int prec, int parity, const double *d_in,
                                    double *d_out, void *stream);
 
+/* 4D domain decomposition (not part of the paper's solver, which runs on one GPU; Sec. 1
+ * mentions the GPU cluster its collaboration runs on).  The lattice global_dims is cut into
+ * grid[0] x grid[1] x grid[2] x grid[3] blocks; each block's extents global_dims/grid must be
+ * even and >= 2.  A part context (dwf_create_part; coord = its block in the grid) holds the
+ * block's sites plus one halo slot per opposite-parity site beyond each cut face.  Before
+ * every hop each part packs the spin projection of its cut faces (Eq. 12 with the
+ * projection of Sec. 3.2: 12 reals per (site, s), half a spinor) and the packed faces are
+ * copied to the neighbouring parts' halos.  dwf_load_gauge_part takes the global gauge field
+ * (host gauge layout of the whole lattice, 72 * V4_global doubles) and keeps the block's
+ * links.  dwf_part_apply applies DWF_OP_DEO, DOE, C, CDAG or CCDAG (precision prec, Schur
+ * parity `parity`) to a global full-lattice host array `in`, the parts -- every block of the
+ * grid exactly once, in any order, on one device or several -- exchanging faces between
+ * the hops, and writes the global result to `out` (sites of the other parity set to 0).
+ * Other calls (dwf_apply_eo*, dwf_solve*, dwf_propagator*) refuse a part context with
+ * DWF_EINVAL.  Errors: DWF_EINVAL (invalid decomposition, parts of different lattices or
+ * operators, a missing or repeated block), DWF_ENOGAUGE, DWF_ENOMEM, DWF_ECUDA. */
+typedef struct {
+    int global_dims[4];   /* whole lattice, Nx, Ny, Nz, Nt */
+    int grid[4];          /* blocks per direction */
+    int coord[4];         /* this part's block, 0 <= coord[mu] < grid[mu] */
+} dwf_partition;
+dwf_status dwf_create_part(const dwf_partition *part, int Ns, double m0, double mq, const double *omega,
+                           const double *sigma, dwf_ctx **out);
+dwf_status dwf_load_gauge_part(dwf_ctx *ctx, const double *U);
+dwf_status dwf_part_apply(int nparts, dwf_ctx *const *parts, int op, int prec, int parity, const double *in,
+                          double *out);
+
 /* The launch shape the autotuner chose for inner-CG kernel class `kclass` (DWF_KC_HOP_M5,
  * DWF_KC_HOP_XPAY or DWF_KC_HOP_UPDATE) at precision `prec` (FP32, F16, BF16) for this
  * context's Ns and volume on its device: *threads per CTA and *persistent (1: a grid of the

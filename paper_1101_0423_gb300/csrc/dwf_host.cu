@@ -708,6 +708,12 @@ dwf_status check_ctx(dwf_ctx *c) {
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// a context of one part of a domain decomposition only works through dwf_part_apply
+dwf_status not_part(dwf_ctx *c) {
+  if (c->part) return fail(c, DWF_EINVAL, "a partitioned context is applied with dwf_part_apply");
+  return DWF_OK;
+}
+
 void begin_profile(dwf_ctx *c, bool on) {
   c->profiling = on;
   c->ev_used = 0;
@@ -867,6 +873,7 @@ dwf_status dwf_destroy(dwf_ctx *c) {
     for (auto &row : c->drec)
       for (void *p : row) dfree(p, c->stream);
     release_gauge(c);
+    dfree(c->d_Ug, c->stream);
     for (int *p : c->d_nbr) dfree(p, c->stream);
     dfree(c->d_sc, c->stream);
     dfree(c->d_part, c->stream);
@@ -883,6 +890,7 @@ dwf_status dwf_destroy(dwf_ctx *c) {
 
 dwf_status dwf_load_gauge_dev(dwf_ctx *c, const double *d_U, void *stream) {
   TRY(check_ctx(c));
+  TRY(not_part(c));
   if (!d_U) return fail(c, DWF_EINVAL, "null gauge pointer");
   cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
   const size_t bytes = (size_t)c->V4 * 72 * sizeof(double);
@@ -903,6 +911,7 @@ dwf_status dwf_load_gauge_dev(dwf_ctx *c, const double *d_U, void *stream) {
 
 dwf_status dwf_load_gauge(dwf_ctx *c, const double *U) {
   TRY(check_ctx(c));
+  TRY(not_part(c));
   if (!U) return fail(c, DWF_EINVAL, "null gauge pointer");
   const size_t bytes = (size_t)c->V4 * 72 * sizeof(double);
   if (c->shared) release_gauge(c);  // back to a private copy
@@ -1016,6 +1025,7 @@ dwf_status dwf_gauge_release(dwf_gauge *g) {
 
 dwf_status dwf_attach_gauge(dwf_ctx *c, dwf_gauge *g) {
   TRY(check_ctx(c));
+  TRY(not_part(c));
   if (!g) return fail(c, DWF_EINVAL, "null gauge handle");
   if (memcmp(g->dims, c->dims, sizeof(c->dims)) != 0) return fail(c, DWF_EINVAL, "gauge lattice differs from the context's");
   if (g->device != c->device) return fail(c, DWF_EINVAL, "gauge field lives on another device");
@@ -1038,6 +1048,7 @@ dwf_status dwf_attach_gauge(dwf_ctx *c, dwf_gauge *g) {
 dwf_status dwf_apply_eo_dev(dwf_ctx *c, int op, int prec, int parity, const double *d_in, double *d_out,
                             void *stream) {
   TRY(check_ctx(c));
+  TRY(not_part(c));
   if (!d_in || !d_out || !aligned16(d_in) || !aligned16(d_out))
     return fail(c, DWF_EINVAL, "null or non-16-byte-aligned field pointer");
   if (!valid_prec(prec)) return fail(c, DWF_EINVAL, "unknown precision");
@@ -1122,6 +1133,7 @@ dwf_status dwf_apply_eo_dev(dwf_ctx *c, int op, int prec, int parity, const doub
 
 dwf_status dwf_apply_eo(dwf_ctx *c, int op, int prec, int parity, const double *in, double *out) {
   TRY(check_ctx(c));
+  TRY(not_part(c));
   if (!in || !out) return fail(c, DWF_EINVAL, "null field pointer");
   const size_t full = (size_t)c->V4 * c->Ns * 24 * sizeof(double);
   void *din, *dout;
@@ -1801,6 +1813,7 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
 
 dwf_status check_solve_args(dwf_ctx *c, dwf_solve_params *prm, const dwf_solve_params *pp, const void *d_rhs,
                             const void *d_sol) {
+  TRY(not_part(c));
   if (pp) *prm = *pp;
   else dwf_solve_params_default(prm);
   if (!d_rhs || !d_sol || !aligned16(d_rhs) || !aligned16(d_sol))
@@ -1966,6 +1979,7 @@ extern "C" dwf_status dwf_solve(dwf_ctx *c, const double *rhs, double *sol, cons
 extern "C" dwf_status dwf_propagator_dev(dwf_ctx *c, const int x0[4], const dwf_solve_params *pp, double *d_prop,
                                          dwf_solve_stats *stats, void *stream) {
   TRY(check_ctx(c));
+  TRY(not_part(c));
   if (!x0 || !d_prop || !aligned16(d_prop)) return fail(c, DWF_EINVAL, "null x0 or non-16-byte-aligned output");
   for (int mu = 0; mu < 4; ++mu)
     if (x0[mu] < 0 || x0[mu] >= c->dims[mu]) return fail(c, DWF_EINVAL, "source point outside the lattice");
@@ -2031,6 +2045,7 @@ size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 extern "C" dwf_status dwf_apply_eo_dev_static(dwf_ctx *c, int op, int prec, int parity, const double *d_in,
                                               double *d_out, void *stream) {
   TRY(check_ctx(c));
+  TRY(not_part(c));
   if (!d_in || !d_out || !aligned16(d_in) || !aligned16(d_out))
     return fail(c, DWF_EINVAL, "null or non-16-byte-aligned field pointer");
   if (!valid_prec(prec)) return fail(c, DWF_EINVAL, "unknown precision");
@@ -2159,5 +2174,320 @@ extern "C" dwf_status dwf_apply_eo_dev_static(dwf_ctx *c, int op, int prec, int 
   CK(cudaMemcpyAsync(&err, &sc->error, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (err) return fail(c, DWF_ETIMEOUT, "a device-side wait for the TMA link copy timed out");
+  return DWF_OK;
+}
+
+// ====================================================================== 4D domain decomposition
+//
+// One context per part of the lattice (dwf_create_part); dwf_part_apply applies an operator
+// to a field spread over all parts: before every hop each part packs the spin projections of
+// its cut faces (12 reals per (site, s)), the packed faces are copied to the neighbouring
+// parts' receive buffers (device to device, or between devices) and unpacked into their
+// halo slots, and each part's hop kernel then runs unchanged with the halo-aware neighbour
+// table.  The fifth-dimension matrices act within a part.
+
+namespace {
+
+template <int P>
+cudaError_t part_gauge_go(dwf_ctx *c, int p, cudaStream_t st) {
+  k_part_gauge<P><<<vec_grid(c->h * 8, c->sm_count), 256, 0, st>>>(
+      c->d_Ug, static_cast<typename PT<P>::lreal *>(c->d_gauge[P][p]), c->pg, p);
+  return cudaGetLastError();
+}
+
+dwf_status ensure_part_gauge(dwf_ctx *c, int prec) {
+  if (!c->d_Ug) return fail(c, DWF_ENOGAUGE, "dwf_load_gauge_part has not been called");
+  if (c->gauge_ready[prec]) return DWF_OK;
+  for (int p = 0; p < 2; ++p) {
+    if (!c->d_gauge[prec][p])
+      CK(dmalloc(&c->d_gauge[prec][p], (size_t)c->h * link_bytes_per_site(prec), c->device, c->stream));
+    switch (prec) {
+      case P_F64: CK(part_gauge_go<P_F64>(c, p, c->stream)); break;
+      case P_F32: CK(part_gauge_go<P_F32>(c, p, c->stream)); break;
+      case P_F16: CK(part_gauge_go<P_F16>(c, p, c->stream)); break;
+      default: CK(part_gauge_go<P_BF16>(c, p, c->stream)); break;
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  c->gauge_ready[prec] = true;
+  c->gauge_loaded = true;
+  return DWF_OK;
+}
+
+// a field of one parity with the halo slots after the local sites
+dwf_status part_field(dwf_ctx *c, const std::string &name, int prec, Field *f) {
+  const size_t n = (size_t)(c->h + c->pg.halo) * c->Ns;
+  void *v = nullptr, *nrm = nullptr;
+  TRY(get_raw(c, "part:" + name + "#" + std::to_string(prec), n * site_bytes(prec), &v));
+  if (prec >= P_F16) TRY(get_raw(c, "part:" + name + "#nrm" + std::to_string(prec), n * sizeof(float), &nrm));
+  f->v = v;
+  f->nrm = static_cast<float *>(nrm);
+  return DWF_OK;
+}
+
+size_t real_bytes(int prec) { return prec == P_F64 ? 8 : 4; }
+
+template <int P>
+cudaError_t part_pack_go(dwf_ctx *c, Field in, int mu, int side, int q, void *buf, cudaStream_t st) {
+  const long n = c->pg.fsz[mu] * c->Ns;
+  k_part_pack<P><<<vec_grid(n, c->sm_count), 256, 0, st>>>(in, c->pg, c->Ns, mu, side, q, side ? 1.0 : -1.0,
+                                                          static_cast<typename PT<P>::real *>(buf));
+  return cudaGetLastError();
+}
+template <int P>
+cudaError_t part_unpack_go(dwf_ctx *c, const void *buf, Field out, long first, long nslot, cudaStream_t st) {
+  k_part_unpack<P><<<vec_grid(nslot * c->Ns, c->sm_count), 256, 0, st>>>(
+      static_cast<const typename PT<P>::real *>(buf), out, first, nslot, c->Ns);
+  return cudaGetLastError();
+}
+cudaError_t part_pack_any(int prec, dwf_ctx *c, Field in, int mu, int side, int q, void *buf, cudaStream_t st) {
+  switch (prec) {
+    case P_F64: return part_pack_go<P_F64>(c, in, mu, side, q, buf, st);
+    case P_F32: return part_pack_go<P_F32>(c, in, mu, side, q, buf, st);
+    case P_F16: return part_pack_go<P_F16>(c, in, mu, side, q, buf, st);
+    default: return part_pack_go<P_BF16>(c, in, mu, side, q, buf, st);
+  }
+}
+cudaError_t part_unpack_any(int prec, dwf_ctx *c, const void *buf, Field out, long first, long nslot,
+                            cudaStream_t st) {
+  switch (prec) {
+    case P_F64: return part_unpack_go<P_F64>(c, buf, out, first, nslot, st);
+    case P_F32: return part_unpack_go<P_F32>(c, buf, out, first, nslot, st);
+    case P_F16: return part_unpack_go<P_F16>(c, buf, out, first, nslot, st);
+    default: return part_unpack_go<P_BF16>(c, buf, out, first, nslot, st);
+  }
+}
+
+// the parts of one decomposed lattice, indexed by their grid coordinates
+struct PartSet {
+  std::vector<dwf_ctx *> at;  // at[x + gx (y + gy (z + gz t))]
+  int grid[4];
+  dwf_ctx *get(const int (&c)[4]) const {
+    int k[4];
+    for (int mu = 0; mu < 4; ++mu) k[mu] = (c[mu] % grid[mu] + grid[mu]) % grid[mu];
+    return at[k[0] + grid[0] * (k[1] + grid[1] * (k[2] + grid[2] * k[3]))];
+  }
+};
+
+// every part's field `name` (parity q) gets its halo slots from the neighbouring parts
+dwf_status part_exchange(const PartSet &ps, const std::string &name, int prec, int q) {
+  // 1. pack the cut faces
+  for (dwf_ctx *c : ps.at) {
+    Field f;
+    TRY(part_field(c, name, prec, &f));
+    for (int mu = 0; mu < 4; ++mu) {
+      if (c->pg.grid[mu] == 1) continue;
+      const size_t bytes = (size_t)c->pg.fsz[mu] * c->Ns * 12 * real_bytes(prec);
+      for (int side = 0; side < 2; ++side) {
+        void *send;
+        TRY(get_raw(c, "part_send" + std::to_string(2 * mu + side), bytes, &send));
+        CK(part_pack_any(prec, c, f, mu, side, q, send, c->stream));
+      }
+    }
+  }
+  for (dwf_ctx *c : ps.at) CK(cudaStreamSynchronize(c->stream));
+  // 2. copy each neighbour's face into this part's receive buffers, 3. unpack into the halo
+  for (dwf_ctx *c : ps.at) {
+    Field f;
+    TRY(part_field(c, name, prec, &f));
+    for (int mu = 0; mu < 4; ++mu) {
+      if (c->pg.grid[mu] == 1) continue;
+      const size_t bytes = (size_t)c->pg.fsz[mu] * c->Ns * 12 * real_bytes(prec);
+      for (int side = 0; side < 2; ++side) {
+        // the upper halo (side 1) holds the upper neighbour's lower face, and vice versa
+        int nc[4] = {c->pg.coord[0], c->pg.coord[1], c->pg.coord[2], c->pg.coord[3]};
+        nc[mu] += side ? 1 : -1;
+        dwf_ctx *n = ps.get(nc);
+        void *send, *recv;
+        TRY(get_raw(n, "part_send" + std::to_string(2 * mu + (1 - side)), bytes, &send));
+        TRY(get_raw(c, "part_recv" + std::to_string(2 * mu + side), bytes, &recv));
+        if (n->device == c->device) CK(cudaMemcpyAsync(recv, send, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        else CK(cudaMemcpyPeerAsync(recv, c->device, send, n->device, bytes, c->stream));
+        CK(part_unpack_any(prec, c, recv, f, c->h + c->pg.foff[mu][side], c->pg.fsz[mu], c->stream));
+      }
+    }
+  }
+  for (dwf_ctx *c : ps.at) CK(cudaStreamSynchronize(c->stream));
+  return DWF_OK;
+}
+
+// one hop stage on every part: out (parity outp) from in (the other parity, halos filled)
+dwf_status part_hop(const PartSet &ps, int prec, int epi, const std::string &in, const std::string &out,
+                    const std::string &y, int outp, int m5, double coef) {
+  TRY(part_exchange(ps, in, prec, 1 - outp));
+  for (dwf_ctx *c : ps.at) {
+    HopArgs a = hop_args(c, prec, outp);
+    TRY(part_field(c, in, prec, &a.in));
+    TRY(part_field(c, out, prec, &a.out));
+    if (!y.empty()) TRY(part_field(c, y, prec, &a.y));
+    if (m5) set_m5(a, c, prec, m5 == 2);
+    a.coef = coef;
+    CK(hop_any(prec, epi, a, c->stream));
+  }
+  return DWF_OK;
+}
+
+}  // namespace
+
+extern "C" dwf_status dwf_create_part(const dwf_partition *pt, int Ns, double m0, double mq, const double *omega,
+                                      const double *sigma, dwf_ctx **out) {
+  if (!pt || !out) return DWF_EINVAL;
+  *out = nullptr;
+  int L[4];
+  for (int mu = 0; mu < 4; ++mu) {
+    if (pt->grid[mu] < 1 || pt->global_dims[mu] < 2 || pt->global_dims[mu] % pt->grid[mu]) return DWF_EINVAL;
+    L[mu] = pt->global_dims[mu] / pt->grid[mu];
+    if (L[mu] < 2 || (L[mu] & 1) || pt->coord[mu] < 0 || pt->coord[mu] >= pt->grid[mu]) return DWF_EINVAL;
+  }
+  dwf_ctx *c = nullptr;
+  TRY(dwf_create(L, Ns, m0, mq, omega, sigma, &c));
+  c->part = true;
+  c->pg = make_part_geom(pt->global_dims, pt->grid, pt->coord);
+  for (int p = 0; p < 2; ++p) k_part_neighbours<0><<<vec_grid(c->h, c->sm_count), 256, 0, c->stream>>>(c->d_nbr[p], c->pg, p);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    dwf_destroy(c);
+    return DWF_ECUDA;
+  }
+  *out = c;
+  return DWF_OK;
+}
+
+extern "C" dwf_status dwf_load_gauge_part(dwf_ctx *c, const double *U) {
+  TRY(check_ctx(c));
+  if (!c->part) return fail(c, DWF_EINVAL, "not a partitioned context");
+  if (!U) return fail(c, DWF_EINVAL, "null gauge pointer");
+  const size_t bytes = (size_t)c->pg.G[0] * c->pg.G[1] * c->pg.G[2] * c->pg.G[3] * 72 * sizeof(double);
+  if (!c->d_Ug) CK(dmalloc((void **)&c->d_Ug, bytes, c->device, c->stream));
+  CK(cudaMemcpyAsync(c->d_Ug, U, bytes, cudaMemcpyHostToDevice, c->stream));
+  for (bool &r : c->gauge_ready) r = false;
+  TRY(ensure_part_gauge(c, P_F64));
+  TRY(ensure_part_gauge(c, P_F32));
+  return DWF_OK;
+}
+
+extern "C" dwf_status dwf_part_apply(int nparts, dwf_ctx *const *parts, int op, int prec, int parity,
+                                     const double *in, double *out) {
+  if (nparts < 1 || !parts || !in || !out) return DWF_EINVAL;
+  dwf_ctx *c0 = parts[0];
+  TRY(check_ctx(c0));
+  if (!valid_prec(prec)) return fail(c0, DWF_EINVAL, "unknown precision");
+  if (op < DWF_OP_DEO || op > DWF_OP_CCDAG || op == DWF_OP_M5 || op == DWF_OP_M5T)
+    return fail(c0, DWF_EINVAL, "dwf_part_apply applies DEO, DOE, C, CDAG or CCDAG");
+  if (op >= DWF_OP_C && parity != 0 && parity != 1) return fail(c0, DWF_EINVAL, "parity must be 0 or 1");
+  PartSet ps;
+  long total = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    ps.grid[mu] = c0->pg.grid[mu];
+    total *= ps.grid[mu];
+  }
+  if (!c0->part || total != nparts) return fail(c0, DWF_EINVAL, "the parts must cover the grid once each");
+  ps.at.assign(nparts, nullptr);
+  for (int k = 0; k < nparts; ++k) {
+    dwf_ctx *c = parts[k];
+    if (!c || !c->part || c->Ns != c0->Ns || c->m0 != c0->m0 || c->mq != c0->mq || c->omega != c0->omega ||
+        c->sigma != c0->sigma || memcmp(c->pg.G, c0->pg.G, sizeof(c->pg.G)) ||
+        memcmp(c->pg.grid, c0->pg.grid, sizeof(c->pg.grid)))
+      return fail(c0, DWF_EINVAL, "parts of different lattices or operators");
+    const int *q = c->pg.coord;
+    dwf_ctx *&slot = ps.at[q[0] + ps.grid[0] * (q[1] + ps.grid[1] * (q[2] + ps.grid[2] * q[3]))];
+    if (slot) return fail(c0, DWF_EINVAL, "two parts at one grid position");
+    slot = c;
+    TRY(check_ctx(c));
+    TRY(ensure_part_gauge(c, prec));
+  }
+  const int Ns = c0->Ns;
+  const int *G = c0->pg.G;
+  const size_t gsite = (size_t)Ns * 24;
+  const int inpar = op == DWF_OP_DEO ? 1 : op == DWF_OP_DOE ? 0 : parity;
+  const int outpar = op == DWF_OP_DEO ? 0 : op == DWF_OP_DOE ? 1 : parity;
+  // every part's share of the global input, in the local host layout, packed on its device
+  std::vector<double> buf;
+  for (dwf_ctx *c : ps.at) {
+    TRY(check_ctx(c));
+    const PartGeom &g = c->pg;
+    buf.assign((size_t)2 * g.h * gsite, 0.0);
+    for (long site = 0; site < 2 * g.h; ++site) {
+      int x[4];
+      long r = site;
+      for (int mu = 0; mu < 4; ++mu) {
+        x[mu] = (int)(r % g.L[mu]) + g.coord[mu] * g.L[mu];
+        r /= g.L[mu];
+      }
+      const size_t gs = x[0] + (size_t)G[0] * (x[1] + (size_t)G[1] * (x[2] + (size_t)G[2] * x[3]));
+      memcpy(&buf[site * gsite], in + gs * gsite, gsite * sizeof(double));
+    }
+    void *d;
+    TRY(get_raw(c, "part_host", buf.size() * sizeof(double), &d));
+    CK(cudaMemcpyAsync(d, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    Field f;
+    TRY(part_field(c, "in", prec, &f));
+    CK(pack_any(prec, static_cast<const double *>(d), f, local_geom(g, Ns), inpar, c->sm_count, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  const int sp = parity, opp = 1 - parity;
+  switch (op) {
+    case DWF_OP_DEO:
+    case DWF_OP_DOE:
+      TRY(part_hop(ps, prec, E_PLAIN, "in", "out", "", outpar, 0, -0.5));
+      break;
+    case DWF_OP_C:  // Eq. 11: u = -1/2 M5 H v; out = v + 1/2 M5 H u
+      TRY(part_hop(ps, prec, E_M, "in", "u", "", opp, 1, -0.5));
+      TRY(part_hop(ps, prec, E_M_XPAY, "u", "out", "in", sp, 1, 0.5));
+      break;
+    case DWF_OP_CDAG:
+    case DWF_OP_CCDAG: {
+      // C^dag v = g5 (1 - D M5^T D M5^T) g5 v: w = M5^T g5 v; t = -1/2 M5^T H w; q = v + 1/2 g5 H t
+      for (dwf_ctx *c : ps.at) {
+        SmixArgs a;
+        memset(&a, 0, sizeof(a));
+        TRY(part_field(c, "in", prec, &a.in));
+        TRY(part_field(c, "w", prec, &a.out));
+        a.K = dmat(c, prec, MK_M5T);
+        a.K2 = dmat(c, prec, MK_ID);
+        a.coef = 1.0;
+        a.h = c->h;
+        a.Ns = Ns;
+        a.sc = c->d_sc;
+        CK(smix_any(prec, S_G5, a, c->stream));
+      }
+      const std::string q = op == DWF_OP_CDAG ? "out" : "q";
+      TRY(part_hop(ps, prec, E_M, "w", "t", "", opp, 2, -0.5));
+      TRY(part_hop(ps, prec, E_XPAY_G5, "t", q, "in", sp, 0, 0.5));
+      if (op == DWF_OP_CCDAG) {
+        TRY(part_hop(ps, prec, E_M, "q", "u", "", opp, 1, -0.5));
+        TRY(part_hop(ps, prec, E_M_XPAY, "u", "out", "q", sp, 1, 0.5));
+      }
+      break;
+    }
+  }
+  // every part's output parity back into the global array
+  const size_t gbytes = (size_t)G[0] * G[1] * G[2] * G[3] * gsite * sizeof(double);
+  memset(out, 0, gbytes);
+  for (dwf_ctx *c : ps.at) {
+    TRY(check_ctx(c));
+    const PartGeom &g = c->pg;
+    void *d;
+    TRY(get_raw(c, "part_host", (size_t)2 * g.h * gsite * sizeof(double), &d));
+    CK(cudaMemsetAsync(d, 0, (size_t)2 * g.h * gsite * sizeof(double), c->stream));
+    Field f;
+    TRY(part_field(c, "out", prec, &f));
+    CK(unpack_any(prec, f, static_cast<double *>(d), local_geom(g, Ns), outpar, c->sm_count, c->stream));
+    buf.assign((size_t)2 * g.h * gsite, 0.0);
+    CK(cudaMemcpyAsync(buf.data(), d, buf.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (long site = 0; site < 2 * g.h; ++site) {
+      int x[4];
+      long r = site;
+      for (int mu = 0; mu < 4; ++mu) {
+        x[mu] = (int)(r % g.L[mu]) + g.coord[mu] * g.L[mu];
+        r /= g.L[mu];
+      }
+      if (((x[0] + x[1] + x[2] + x[3]) & 1) != outpar) continue;
+      const size_t gs = x[0] + (size_t)G[0] * (x[1] + (size_t)G[1] * (x[2] + (size_t)G[2] * x[3]));
+      memcpy(out + gs * gsite, &buf[site * gsite], gsite * sizeof(double));
+    }
+  }
   return DWF_OK;
 }

@@ -10,6 +10,7 @@
 
 #include "../../include/dwf.h"
 #include "dwf_launch.cuh"
+#include "dwf_part.cuh"
 #include "dwf_tune.h"
 
 namespace dwf {
@@ -99,6 +100,11 @@ struct dwf_ctx {
   // the launches of the current call take the autotuner's shapes (off for a solve with
   // no_autotune, which keeps the default shapes)
   bool use_tuned = true;
+  // one part of a 4D domain decomposition (dwf_create_part): halo layout, the global gauge
+  // field its local links are read from
+  bool part = false;
+  dwf::PartGeom pg{};
+  double *d_Ug = nullptr;
   // profiling of the current call
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;

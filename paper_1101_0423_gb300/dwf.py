@@ -60,6 +60,10 @@ class SolveStats(ctypes.Structure):
         return d
 
 
+class Partition(ctypes.Structure):
+    _fields_ = [("global_dims", ctypes.c_int * 4), ("grid", ctypes.c_int * 4), ("coord", ctypes.c_int * 4)]
+
+
 class ServerParams(ctypes.Structure):
     _fields_ = [("hbm_budget_gb", ctypes.c_double), ("max_inflight", ctypes.c_int),
                 ("max_batch", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
@@ -136,6 +140,9 @@ def load(build_if_missing: bool = True):
         "dwf_optimal_weights": ([i, d, d, dp, dp], i),
         "dwf_debug_set_wait": ([vp, ctypes.c_uint, i], i),
         "dwf_tuned_shape": ([vp, i, i, ip, ip], i),
+        "dwf_create_part": ([ctypes.POINTER(Partition), i, d, d, dp, dp, ctypes.POINTER(vp)], i),
+        "dwf_load_gauge_part": ([vp, dp], i),
+        "dwf_part_apply": ([i, ctypes.POINTER(vp), i, i, i, dp, dp], i),
         "dwf_cancel": ([vp, ctypes.c_uint64], i),
         "dwf_server_set_admission": ([vp, i], i),
     }
@@ -343,6 +350,32 @@ def dwf_tuned_shape(ctx, prec, kclass):
     if st not in (DWF_OK, DWF_EAGAIN):
         _check(ctx, st)
     return t.value, bool(p.value), st == DWF_OK
+
+
+def dwf_create_part(global_dims, grid, coord, Ns, m0, mq, omega, sigma):
+    """A context for the block `coord` of a 4D domain decomposition (opaque handle)."""
+    omega, sigma = _f64(omega), _f64(sigma)
+    pt = Partition((ctypes.c_int * 4)(*global_dims), (ctypes.c_int * 4)(*grid), (ctypes.c_int * 4)(*coord))
+    out = ctypes.c_void_p()
+    st = load().dwf_create_part(ctypes.byref(pt), int(Ns), float(m0), float(mq), _dp(omega), _dp(sigma),
+                                ctypes.byref(out))
+    if st != DWF_OK:
+        raise DwfError(st, "dwf_create_part rejected the decomposition or could not allocate")
+    return out.value
+
+
+def dwf_load_gauge_part(ctx, U_global):
+    U_global = _f64(U_global)
+    _check(ctx, load().dwf_load_gauge_part(ctx, _dp(U_global)))
+
+
+def dwf_part_apply(parts, op, prec, parity, x) -> np.ndarray:
+    """Applies op to the global host array x across all parts (faces exchanged between hops)."""
+    x = _f64(x)
+    out = np.empty_like(x)
+    arr = (ctypes.c_void_p * len(parts))(*parts)
+    _check(parts[0], load().dwf_part_apply(len(parts), arr, int(op), int(prec), int(parity), _dp(x), _dp(out)))
+    return out
 
 
 def dwf_last_error(ctx) -> str:
