@@ -290,6 +290,17 @@ dwf_status dwf_create_part(const dwf_partition *part, int Ns, double m0, double 
 dwf_status dwf_load_gauge_part(dwf_ctx *ctx, const double *U);
 dwf_status dwf_part_apply(int nparts, dwf_ctx *const *parts, int op, int prec, int parity, const double *in,
                           double *out);
+/* Solve across the parts: the same system as dwf_solve (params->system: D psi = eta with
+ * rhs = eta, or C C^dag x = b on params->schur_parity) for a global full-lattice host rhs,
+ * the solution written to the global host array sol.  Inner CG (Algorithm 1) in
+ * params->inner_prec with FP64 reliable updates (Sec. 2.3: restart when |r| falls by
+ * params->delta, default 0.01, or reaches the target), every reduction summed over the
+ * parts in FP64 (the allreduce of a multi-GPU run: 2 per iteration), faces exchanged before
+ * every hop.  The host steers each iteration (no CUDA graphs) and a full solve takes no
+ * tightened second pass: DWF_ENOCONV if |eta - D psi| / |eta| misses tol.  stats (if not
+ * NULL): iterations, restarts, true residuals (FP64), counted flops, host wall time. */
+dwf_status dwf_part_solve(int nparts, dwf_ctx *const *parts, const double *rhs, double *sol,
+                          const dwf_solve_params *params, dwf_solve_stats *stats);
 
 /* The launch shape the autotuner chose for inner-CG kernel class `kclass` (DWF_KC_HOP_M5,
  * DWF_KC_HOP_XPAY or DWF_KC_HOP_UPDATE) at precision `prec` (FP32, F16, BF16) for this

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <map>
 #include <string>
 #include <vector>
@@ -132,6 +133,8 @@ dwf_status fail(dwf_ctx *c, dwf_status st, const std::string &msg) {
   } while (0)
 
 size_t site_bytes(int prec) { return prec == P_F64 ? 192 : prec == P_F32 ? 96 : 48; }
+// precision of the inner CG's x (FP32 when the inner fields are 16-bit, see k_smix)
+int xprec(int prec) { return prec >= P_F16 ? P_F32 : prec; }
 int mat_index(int prec) { return prec == P_F64 ? 0 : 1; }
 bool valid_prec(int p) { return p >= DWF_PREC_F64 && p <= DWF_PREC_BF16; }
 
@@ -1270,6 +1273,7 @@ dwf_status cg_iteration(dwf_ctx *c, cudaStream_t st, const SolveState &S, const 
     m.r = S.r;
     m.p = S.p;
     m.x = S.x;
+    m.xfstride = field_bytes(c, xprec(P));
     m.K = dmat(c, P, MK_M5T);
     m.K2 = dmat(c, P, MK_ID);
     m.coef = 1.0;
@@ -1381,7 +1385,7 @@ dwf_status tune_inner(dwf_ctx *c, cudaStream_t st, const SolveState &S) {
 // r_hat = b - C C^dag x_hat, |r_hat|^2 -> red, r = r_hat in the inner precision, |r|^2 -> red2
 dwf_status fp64_restart(dwf_ctx *c, cudaStream_t st, const SolveState &S, int k) {
   const Field xh = at(c, S.xh, k, P_F64), rh = at(c, S.rh, k, P_F64), bk = at(c, S.b, k, P_F64);
-  const Field x = at(c, S.x, k, S.prec), r = at(c, S.r, k, S.prec);
+  const Field x = at(c, S.x, k, xprec(S.prec)), r = at(c, S.r, k, S.prec);
   {
     VecArgs v;
     memset(&v, 0, sizeof(v));
@@ -1473,7 +1477,7 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
   TRY(get_buf(c, "q64", P_F64, &S.q64));
   TRY(get_buf(c, "u64", P_F64, &S.u64));
   auto inner_bufs = [&]() -> dwf_status {
-    TRY(get_buf_k(c, "cg_x", S.prec, K, &S.x));
+    TRY(get_buf_k(c, "cg_x", xprec(S.prec), K, &S.x));
     TRY(get_buf_k(c, "cg_r", S.prec, K, &S.r));
     TRY(get_buf_k(c, "cg_p", S.prec, K, &S.p));
     TRY(get_buf_k(c, "cg_q", S.prec, K, &S.q));
@@ -1556,12 +1560,9 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
 
   // ---- source: b_k on the Schur parity (Eq. 10 for the full system); x_hat = 0, r_hat = b,
   // r = b in the inner precision, x = p = 0
-  CK(cudaMemsetAsync(S.x.v, 0, (size_t)K * field_bytes(c, S.prec), st));
+  CK(cudaMemsetAsync(S.x.v, 0, (size_t)K * field_bytes(c, xprec(S.prec)), st));
   CK(cudaMemsetAsync(S.p.v, 0, (size_t)K * field_bytes(c, S.prec), st));
-  if (S.x.nrm) {
-    CK(cudaMemsetAsync(S.x.nrm, 0, (size_t)K * c->h * c->Ns * sizeof(float), st));
-    CK(cudaMemsetAsync(S.p.nrm, 0, (size_t)K * c->h * c->Ns * sizeof(float), st));
-  }
+  if (S.p.nrm) CK(cudaMemsetAsync(S.p.nrm, 0, (size_t)K * c->h * c->Ns * sizeof(float), st));
   CK(cudaMemsetAsync(S.xh.v, 0, (size_t)K * nbytes64, st));
   for (int k = 0; k < K; ++k) {
     UseSlot use(c, sl, k);
@@ -1684,7 +1685,7 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
           TRY(ensure_gauge(c, P_F32, st));
           S.prec = P_F32;
           TRY(inner_bufs());
-          CK(cudaMemsetAsync(S.x.v, 0, field_bytes(c, S.prec), st));
+          CK(cudaMemsetAsync(S.x.v, 0, field_bytes(c, xprec(S.prec)), st));
           CK(cudaMemsetAsync(S.p.v, 0, field_bytes(c, S.prec), st));
           TRY(convert(c, st, P_F64, S.rh, S.prec, S.r, DWF_KC_F64));
           TRY(norm2(c, st, S.prec, S.r, FIN_RED2));
@@ -2311,18 +2312,129 @@ dwf_status part_exchange(const PartSet &ps, const std::string &name, int prec, i
   return DWF_OK;
 }
 
-// one hop stage on every part: out (parity outp) from in (the other parity, halos filled)
+// one hop stage on every part: out (parity outp) from in (the other parity, halos filled);
+// m5: 0 none, 1 M5, 2 M5^T; optional operand fields y, r (updated in place) and b, and the
+// reduction's result slot fin (each part's own sum; the caller adds the parts' sums)
+struct PartHop {
+  int epi;
+  std::string in, out, y, r, b;
+  int outp, m5;
+  double coef;
+  int fin = FIN_NONE;
+};
+dwf_status part_hop(const PartSet &ps, int prec, const PartHop &h) {
+  TRY(part_exchange(ps, h.in, prec, 1 - h.outp));
+  for (dwf_ctx *c : ps.at) {
+    HopArgs a = hop_args(c, prec, h.outp);
+    TRY(part_field(c, h.in, prec, &a.in));
+    if (!h.out.empty()) TRY(part_field(c, h.out, prec, &a.out));
+    if (!h.y.empty()) TRY(part_field(c, h.y, prec, &a.y));
+    if (!h.r.empty()) TRY(part_field(c, h.r, prec, &a.r));
+    if (!h.b.empty()) TRY(part_field(c, h.b, prec, &a.b));
+    if (h.m5) set_m5(a, c, prec, h.m5 == 2);
+    a.coef = h.coef;
+    a.fin = h.fin;
+    CK(hop_any(prec, h.epi, a, c->stream));
+  }
+  return DWF_OK;
+}
 dwf_status part_hop(const PartSet &ps, int prec, int epi, const std::string &in, const std::string &out,
                     const std::string &y, int outp, int m5, double coef) {
-  TRY(part_exchange(ps, in, prec, 1 - outp));
+  PartHop h;
+  h.epi = epi;
+  h.in = in;
+  h.out = out;
+  h.y = y;
+  h.outp = outp;
+  h.m5 = m5;
+  h.coef = coef;
+  return part_hop(ps, prec, h);
+}
+
+// the parts of one decomposed lattice, checked: the same lattice, grid and operator, every
+// block exactly once; the gauge forms of precisions prec (and FP64) built
+dwf_status part_set(int nparts, dwf_ctx *const *parts, int prec, PartSet *ps) {
+  dwf_ctx *c0 = parts[0];
+  long total = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    ps->grid[mu] = c0->pg.grid[mu];
+    total *= ps->grid[mu];
+  }
+  if (!c0->part || total != nparts) return fail(c0, DWF_EINVAL, "the parts must cover the grid once each");
+  ps->at.assign(nparts, nullptr);
+  for (int k = 0; k < nparts; ++k) {
+    dwf_ctx *c = parts[k];
+    if (!c || !c->part || c->Ns != c0->Ns || c->m0 != c0->m0 || c->mq != c0->mq || c->omega != c0->omega ||
+        c->sigma != c0->sigma || memcmp(c->pg.G, c0->pg.G, sizeof(c->pg.G)) ||
+        memcmp(c->pg.grid, c0->pg.grid, sizeof(c->pg.grid)))
+      return fail(c0, DWF_EINVAL, "parts of different lattices or operators");
+    const int *q = c->pg.coord;
+    dwf_ctx *&slot = ps->at[q[0] + ps->grid[0] * (q[1] + ps->grid[1] * (q[2] + ps->grid[2] * q[3]))];
+    if (slot) return fail(c0, DWF_EINVAL, "two parts at one grid position");
+    slot = c;
+    TRY(check_ctx(c));
+    TRY(ensure_part_gauge(c, prec));
+    TRY(ensure_part_gauge(c, P_F64));
+  }
+  return DWF_OK;
+}
+
+// every part's share of a global full-lattice host array into its field `name` (parity p)
+dwf_status part_scatter(const PartSet &ps, const double *g_in, const std::string &name, int prec, int p) {
+  std::vector<double> buf;
   for (dwf_ctx *c : ps.at) {
-    HopArgs a = hop_args(c, prec, outp);
-    TRY(part_field(c, in, prec, &a.in));
-    TRY(part_field(c, out, prec, &a.out));
-    if (!y.empty()) TRY(part_field(c, y, prec, &a.y));
-    if (m5) set_m5(a, c, prec, m5 == 2);
-    a.coef = coef;
-    CK(hop_any(prec, epi, a, c->stream));
+    TRY(check_ctx(c));
+    const PartGeom &g = c->pg;
+    const size_t gsite = (size_t)c->Ns * 24;
+    buf.assign((size_t)2 * g.h * gsite, 0.0);
+    for (long site = 0; site < 2 * g.h; ++site) {
+      int x[4];
+      long r = site;
+      for (int mu = 0; mu < 4; ++mu) {
+        x[mu] = (int)(r % g.L[mu]) + g.coord[mu] * g.L[mu];
+        r /= g.L[mu];
+      }
+      const size_t gs = x[0] + (size_t)g.G[0] * (x[1] + (size_t)g.G[1] * (x[2] + (size_t)g.G[2] * x[3]));
+      memcpy(&buf[site * gsite], g_in + gs * gsite, gsite * sizeof(double));
+    }
+    void *d;
+    TRY(get_raw(c, "part_host", buf.size() * sizeof(double), &d));
+    CK(cudaMemcpyAsync(d, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    Field f;
+    TRY(part_field(c, name, prec, &f));
+    CK(pack_any(prec, static_cast<const double *>(d), f, local_geom(g, c->Ns), p, c->sm_count, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return DWF_OK;
+}
+
+// every part's field `name` (parity p) into the global host array (its sites of parity p)
+dwf_status part_gather(const PartSet &ps, const std::string &name, int prec, int p, double *g_out) {
+  std::vector<double> buf;
+  for (dwf_ctx *c : ps.at) {
+    TRY(check_ctx(c));
+    const PartGeom &g = c->pg;
+    const size_t gsite = (size_t)c->Ns * 24;
+    void *d;
+    TRY(get_raw(c, "part_host", (size_t)2 * g.h * gsite * sizeof(double), &d));
+    CK(cudaMemsetAsync(d, 0, (size_t)2 * g.h * gsite * sizeof(double), c->stream));
+    Field f;
+    TRY(part_field(c, name, prec, &f));
+    CK(unpack_any(prec, f, static_cast<double *>(d), local_geom(g, c->Ns), p, c->sm_count, c->stream));
+    buf.assign((size_t)2 * g.h * gsite, 0.0);
+    CK(cudaMemcpyAsync(buf.data(), d, buf.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (long site = 0; site < 2 * g.h; ++site) {
+      int x[4];
+      long r = site;
+      for (int mu = 0; mu < 4; ++mu) {
+        x[mu] = (int)(r % g.L[mu]) + g.coord[mu] * g.L[mu];
+        r /= g.L[mu];
+      }
+      if (((x[0] + x[1] + x[2] + x[3]) & 1) != p) continue;
+      const size_t gs = x[0] + (size_t)g.G[0] * (x[1] + (size_t)g.G[1] * (x[2] + (size_t)g.G[2] * x[3]));
+      memcpy(g_out + gs * gsite, &buf[site * gsite], gsite * sizeof(double));
+    }
   }
   return DWF_OK;
 }
@@ -2369,7 +2481,7 @@ extern "C" dwf_status dwf_load_gauge_part(dwf_ctx *c, const double *U) {
 
 extern "C" dwf_status dwf_part_apply(int nparts, dwf_ctx *const *parts, int op, int prec, int parity,
                                      const double *in, double *out) {
-  if (nparts < 1 || !parts || !in || !out) return DWF_EINVAL;
+  if (nparts < 1 || !parts || !parts[0] || !in || !out) return DWF_EINVAL;
   dwf_ctx *c0 = parts[0];
   TRY(check_ctx(c0));
   if (!valid_prec(prec)) return fail(c0, DWF_EINVAL, "unknown precision");
@@ -2377,55 +2489,10 @@ extern "C" dwf_status dwf_part_apply(int nparts, dwf_ctx *const *parts, int op, 
     return fail(c0, DWF_EINVAL, "dwf_part_apply applies DEO, DOE, C, CDAG or CCDAG");
   if (op >= DWF_OP_C && parity != 0 && parity != 1) return fail(c0, DWF_EINVAL, "parity must be 0 or 1");
   PartSet ps;
-  long total = 1;
-  for (int mu = 0; mu < 4; ++mu) {
-    ps.grid[mu] = c0->pg.grid[mu];
-    total *= ps.grid[mu];
-  }
-  if (!c0->part || total != nparts) return fail(c0, DWF_EINVAL, "the parts must cover the grid once each");
-  ps.at.assign(nparts, nullptr);
-  for (int k = 0; k < nparts; ++k) {
-    dwf_ctx *c = parts[k];
-    if (!c || !c->part || c->Ns != c0->Ns || c->m0 != c0->m0 || c->mq != c0->mq || c->omega != c0->omega ||
-        c->sigma != c0->sigma || memcmp(c->pg.G, c0->pg.G, sizeof(c->pg.G)) ||
-        memcmp(c->pg.grid, c0->pg.grid, sizeof(c->pg.grid)))
-      return fail(c0, DWF_EINVAL, "parts of different lattices or operators");
-    const int *q = c->pg.coord;
-    dwf_ctx *&slot = ps.at[q[0] + ps.grid[0] * (q[1] + ps.grid[1] * (q[2] + ps.grid[2] * q[3]))];
-    if (slot) return fail(c0, DWF_EINVAL, "two parts at one grid position");
-    slot = c;
-    TRY(check_ctx(c));
-    TRY(ensure_part_gauge(c, prec));
-  }
-  const int Ns = c0->Ns;
-  const int *G = c0->pg.G;
-  const size_t gsite = (size_t)Ns * 24;
+  TRY(part_set(nparts, parts, prec, &ps));
   const int inpar = op == DWF_OP_DEO ? 1 : op == DWF_OP_DOE ? 0 : parity;
   const int outpar = op == DWF_OP_DEO ? 0 : op == DWF_OP_DOE ? 1 : parity;
-  // every part's share of the global input, in the local host layout, packed on its device
-  std::vector<double> buf;
-  for (dwf_ctx *c : ps.at) {
-    TRY(check_ctx(c));
-    const PartGeom &g = c->pg;
-    buf.assign((size_t)2 * g.h * gsite, 0.0);
-    for (long site = 0; site < 2 * g.h; ++site) {
-      int x[4];
-      long r = site;
-      for (int mu = 0; mu < 4; ++mu) {
-        x[mu] = (int)(r % g.L[mu]) + g.coord[mu] * g.L[mu];
-        r /= g.L[mu];
-      }
-      const size_t gs = x[0] + (size_t)G[0] * (x[1] + (size_t)G[1] * (x[2] + (size_t)G[2] * x[3]));
-      memcpy(&buf[site * gsite], in + gs * gsite, gsite * sizeof(double));
-    }
-    void *d;
-    TRY(get_raw(c, "part_host", buf.size() * sizeof(double), &d));
-    CK(cudaMemcpyAsync(d, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    Field f;
-    TRY(part_field(c, "in", prec, &f));
-    CK(pack_any(prec, static_cast<const double *>(d), f, local_geom(g, Ns), inpar, c->sm_count, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-  }
+  TRY(part_scatter(ps, in, "in", prec, inpar));
   const int sp = parity, opp = 1 - parity;
   switch (op) {
     case DWF_OP_DEO:
@@ -2440,17 +2507,10 @@ extern "C" dwf_status dwf_part_apply(int nparts, dwf_ctx *const *parts, int op, 
     case DWF_OP_CCDAG: {
       // C^dag v = g5 (1 - D M5^T D M5^T) g5 v: w = M5^T g5 v; t = -1/2 M5^T H w; q = v + 1/2 g5 H t
       for (dwf_ctx *c : ps.at) {
-        SmixArgs a;
-        memset(&a, 0, sizeof(a));
-        TRY(part_field(c, "in", prec, &a.in));
-        TRY(part_field(c, "w", prec, &a.out));
-        a.K = dmat(c, prec, MK_M5T);
-        a.K2 = dmat(c, prec, MK_ID);
-        a.coef = 1.0;
-        a.h = c->h;
-        a.Ns = Ns;
-        a.sc = c->d_sc;
-        CK(smix_any(prec, S_G5, a, c->stream));
+        Field fi, fw;
+        TRY(part_field(c, "in", prec, &fi));
+        TRY(part_field(c, "w", prec, &fw));
+        TRY(smix(c, c->stream, prec, S_G5, fi, fw, MK_M5T, 1.0, DWF_KC_OTHER));
       }
       const std::string q = op == DWF_OP_CDAG ? "out" : "q";
       TRY(part_hop(ps, prec, E_M, "w", "t", "", opp, 2, -0.5));
@@ -2462,32 +2522,285 @@ extern "C" dwf_status dwf_part_apply(int nparts, dwf_ctx *const *parts, int op, 
       break;
     }
   }
-  // every part's output parity back into the global array
-  const size_t gbytes = (size_t)G[0] * G[1] * G[2] * G[3] * gsite * sizeof(double);
-  memset(out, 0, gbytes);
+  const int *G = c0->pg.G;
+  memset(out, 0, (size_t)G[0] * G[1] * G[2] * G[3] * c0->Ns * 24 * sizeof(double));
+  return part_gather(ps, "out", prec, outpar, out);
+}
+
+namespace {
+
+// the parts' reduction results added over the parts (the allreduce of a multi-GPU run):
+// slot 0 = red, 1 = red2 of every part's scalar block
+dwf_status part_sum(const PartSet &ps, int slot, double *out) {
+  double s = 0;
   for (dwf_ctx *c : ps.at) {
-    TRY(check_ctx(c));
-    const PartGeom &g = c->pg;
-    void *d;
-    TRY(get_raw(c, "part_host", (size_t)2 * g.h * gsite * sizeof(double), &d));
-    CK(cudaMemsetAsync(d, 0, (size_t)2 * g.h * gsite * sizeof(double), c->stream));
+    TRY(pull_scalars(c, c->stream));
+    s += slot ? c->h_sc->red2 : c->h_sc->red;
+  }
+  *out = s;
+  return DWF_OK;
+}
+
+// alpha and beta of the inner CG to every part's scalar block
+dwf_status part_set_ab(const PartSet &ps, double alpha, double beta) {
+  for (dwf_ctx *c : ps.at) {
+    CGScalars &h = *c->h_sc;
+    h.alpha = alpha;
+    h.alpha_f = (float)alpha;
+    h.beta = beta;
+    h.beta_f = (float)beta;
+    h.restart_flag = 0;
+    TRY(push_scalars(c, c->stream));
+  }
+  return DWF_OK;
+}
+
+dwf_status part_norm2(const PartSet &ps, const std::string &name, int prec, double *out) {
+  for (dwf_ctx *c : ps.at) {
     Field f;
-    TRY(part_field(c, "out", prec, &f));
-    CK(unpack_any(prec, f, static_cast<double *>(d), local_geom(g, Ns), outpar, c->sm_count, c->stream));
-    buf.assign((size_t)2 * g.h * gsite, 0.0);
-    CK(cudaMemcpyAsync(buf.data(), d, buf.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    for (long site = 0; site < 2 * g.h; ++site) {
-      int x[4];
-      long r = site;
-      for (int mu = 0; mu < 4; ++mu) {
-        x[mu] = (int)(r % g.L[mu]) + g.coord[mu] * g.L[mu];
-        r /= g.L[mu];
+    TRY(part_field(c, name, prec, &f));
+    TRY(norm2(c, c->stream, prec, f, FIN_RED));
+  }
+  return part_sum(ps, 0, out);
+}
+
+// rh = b - C C^dag xh in FP64 on Schur parity sp, |rh|^2 over all parts (Eq. 11)
+dwf_status part_resid64(const PartSet &ps, int sp, double *rr) {
+  for (dwf_ctx *c : ps.at) {
+    Field x, w;
+    TRY(part_field(c, "xh", P_F64, &x));
+    TRY(part_field(c, "w64", P_F64, &w));
+    TRY(smix(c, c->stream, P_F64, S_G5, x, w, MK_M5T, 1.0, DWF_KC_F64));
+  }
+  TRY(part_hop(ps, P_F64, E_M, "w64", "t64", "", 1 - sp, 2, -0.5));
+  TRY(part_hop(ps, P_F64, E_XPAY_G5, "t64", "q64", "xh", sp, 0, 0.5));
+  TRY(part_hop(ps, P_F64, E_M, "q64", "u64", "", 1 - sp, 1, -0.5));
+  PartHop h;
+  h.epi = E_RESID;
+  h.in = "u64";
+  h.out = "rh";
+  h.y = "q64";
+  h.b = "b";
+  h.outp = sp;
+  h.m5 = 1;
+  h.coef = 0.5;
+  h.fin = FIN_RED;
+  TRY(part_hop(ps, P_F64, h));
+  return part_sum(ps, 0, rr);
+}
+
+}  // namespace
+
+extern "C" dwf_status dwf_part_solve(int nparts, dwf_ctx *const *parts, const double *rhs, double *sol,
+                                     const dwf_solve_params *pp, dwf_solve_stats *stats) {
+  if (nparts < 1 || !parts || !parts[0] || !rhs || !sol) return DWF_EINVAL;
+  dwf_ctx *c0 = parts[0];
+  TRY(check_ctx(c0));
+  dwf_solve_params prm;
+  if (pp) prm = *pp;
+  else dwf_solve_params_default(&prm);
+  if (!(prm.tol > 0.0) || !valid_prec(prm.inner_prec) || (prm.system != DWF_SYS_FULL && prm.system != DWF_SYS_NORMAL) ||
+      (prm.schur_parity != 0 && prm.schur_parity != 1) || prm.max_iter < 1)
+    return fail(c0, DWF_EINVAL, "invalid solve parameters");
+  const int P = prm.inner_prec, sp = prm.schur_parity, opp = 1 - sp;
+  const bool full = prm.system == DWF_SYS_FULL;
+  const double delta = prm.delta > 0.0 ? prm.delta : 0.01;
+  PartSet ps;
+  TRY(part_set(nparts, parts, P, &ps));
+  const auto t0 = std::chrono::steady_clock::now();
+  // ---- the Schur-parity source (Eq. 10 for the full system): b = eta'_sp - M5 D eta'_op
+  if (full) {
+    for (int p = 0; p < 2; ++p) TRY(part_scatter(ps, rhs, "eta" + std::to_string(p), P_F64, p));
+    for (dwf_ctx *c : ps.at)
+      for (int p = 0; p < 2; ++p) {
+        Field e, ep;
+        TRY(part_field(c, "eta" + std::to_string(p), P_F64, &e));
+        TRY(part_field(c, "etap" + std::to_string(p), P_F64, &ep));
+        TRY(smix(c, c->stream, P_F64, S_PLAIN, e, ep, MK_S1, 1.0, DWF_KC_F64));
       }
-      if (((x[0] + x[1] + x[2] + x[3]) & 1) != outpar) continue;
-      const size_t gs = x[0] + (size_t)G[0] * (x[1] + (size_t)G[1] * (x[2] + (size_t)G[2] * x[3]));
-      memcpy(out + gs * gsite, &buf[site * gsite], gsite * sizeof(double));
+    TRY(part_hop(ps, P_F64, E_M_XPAY, "etap" + std::to_string(opp), "b", "etap" + std::to_string(sp), sp, 1, 0.5));
+  } else {
+    TRY(part_scatter(ps, rhs, "b", P_F64, sp));
+  }
+  double bnorm2 = 0;
+  TRY(part_norm2(ps, "b", P_F64, &bnorm2));
+  const double tol_schur = full ? 0.01 * (prm.schur_target_pct > 0 ? prm.schur_target_pct : 50) * prm.tol : prm.tol;
+  // x_hat = 0, r_hat = b, r = b in the inner precision, x = p = 0
+  for (dwf_ctx *c : ps.at) {
+    Field xh, rh, b, x, p, r;
+    TRY(part_field(c, "xh", P_F64, &xh));
+    TRY(part_field(c, "rh", P_F64, &rh));
+    TRY(part_field(c, "b", P_F64, &b));
+    TRY(part_field(c, "cg_x", xprec(P), &x));
+    TRY(part_field(c, "cg_p", P, &p));
+    TRY(part_field(c, "cg_r", P, &r));
+    const size_t n = (size_t)c->h * c->Ns;
+    CK(cudaMemsetAsync(xh.v, 0, n * site_bytes(P_F64), c->stream));
+    CK(cudaMemcpyAsync(rh.v, b.v, n * site_bytes(P_F64), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemsetAsync(x.v, 0, n * site_bytes(xprec(P)), c->stream));
+    CK(cudaMemsetAsync(p.v, 0, n * site_bytes(P), c->stream));
+    if (p.nrm) CK(cudaMemsetAsync(p.nrm, 0, n * sizeof(float), c->stream));
+    TRY(convert(c, c->stream, P_F64, b, P, r, DWF_KC_OTHER));
+  }
+  double rr = 0;
+  TRY(part_norm2(ps, "cg_r", P, &rr));
+  double rhat2 = bnorm2, rmax = rr, alpha = 0, beta = 0;
+  int iters = 0, restarts = 0;
+  bool converged = bnorm2 == 0.0;
+  // ---- mixed-precision CG on C C^dag (Algorithm 1) with FP64 reliable updates (Sec. 2.3),
+  // the global sums of every reduction taken over the parts
+  while (!converged && iters < prm.max_iter) {
+    TRY(part_set_ab(ps, alpha, beta));
+    for (dwf_ctx *c : ps.at) {  // x += alpha p (the previous step), p = r + beta p, w = M5^T g5 p
+      SmixArgs m;
+      memset(&m, 0, sizeof(m));
+      TRY(part_field(c, "cg_w", P, &m.out));
+      TRY(part_field(c, "cg_r", P, &m.r));
+      TRY(part_field(c, "cg_p", P, &m.p));
+      TRY(part_field(c, "cg_x", xprec(P), &m.x));
+      m.K = dmat(c, P, MK_M5T);
+      m.K2 = dmat(c, P, MK_ID);
+      m.coef = 1.0;
+      m.h = c->h;
+      m.Ns = c->Ns;
+      m.sc = c->d_sc;
+      CK(smix_any(P, S_CGP, m, c->stream));
+    }
+    TRY(part_hop(ps, P, E_M, "cg_w", "cg_t", "", opp, 2, -0.5));
+    PartHop xq;
+    xq.epi = E_XPAY_G5;
+    xq.in = "cg_t";
+    xq.out = "cg_q";
+    xq.y = "cg_p";
+    xq.outp = sp;
+    xq.m5 = 0;
+    xq.coef = 0.5;
+    xq.fin = FIN_RED;
+    TRY(part_hop(ps, P, xq));
+    double qq = 0;
+    TRY(part_sum(ps, 0, &qq));
+    alpha = rr / qq;  // (r, r) / (p, A p), (p, A p) = |C^dag p|^2
+    TRY(part_set_ab(ps, alpha, beta));
+    TRY(part_hop(ps, P, E_M, "cg_q", "cg_u", "", opp, 1, -0.5));
+    PartHop up;
+    up.epi = E_CG_UPDATE;
+    up.in = "cg_u";
+    up.y = "cg_q";
+    up.r = "cg_r";
+    up.outp = sp;
+    up.m5 = 1;
+    up.coef = 0.5;
+    up.fin = FIN_RED2;
+    TRY(part_hop(ps, P, up));  // r -= alpha (q + 1/2 M5 H u), |r|^2
+    double rr_new = 0;
+    TRY(part_sum(ps, 1, &rr_new));
+    ++iters;
+    beta = rr_new / rr;
+    const double rr_prev = rr;
+    rr = rr_new;
+    rmax = std::max(rmax, rr);
+    if (!(rr > tol_schur * tol_schur * bnorm2) || !(rr > delta * delta * rmax) || iters >= prm.max_iter) {
+      // FP64 restart: x_hat += x + alpha p, x = 0; r_hat = b - C C^dag x_hat; r = r_hat
+      for (dwf_ctx *c : ps.at) {
+        VecArgs v;
+        memset(&v, 0, sizeof(v));
+        TRY(part_field(c, "xh", P_F64, &v.a));
+        TRY(part_field(c, "cg_x", xprec(P), &v.b));
+        TRY(part_field(c, "cg_p", P, &v.c));
+        v.sc = c->d_sc;
+        v.n = c->h * c->Ns;
+        v.Ns = c->Ns;
+        CK(accum_any(P, v, c->sm_count, c->stream));
+      }
+      TRY(part_resid64(ps, sp, &rhat2));
+      ++restarts;
+      for (dwf_ctx *c : ps.at) {
+        Field rh, r;
+        TRY(part_field(c, "rh", P_F64, &rh));
+        TRY(part_field(c, "cg_r", P, &r));
+        TRY(convert(c, c->stream, P_F64, rh, P, r, DWF_KC_F64));
+      }
+      TRY(part_norm2(ps, "cg_r", P, &rr));
+      converged = rhat2 <= tol_schur * tol_schur * bnorm2;
+      // reliable update: keep p, beta from the recomputed residual; the pending step is in x_hat
+      beta = rr / rr_prev;
+      alpha = 0;
+      rmax = rr;
     }
   }
+  double res_full = 0;
+  if (full) {
+    // phi_sp = C^dag x_hat; phi_op = eta'_op - M5 D phi_sp; psi = S2 phi (Eq. 9-10)
+    for (dwf_ctx *c : ps.at) {
+      Field x, w;
+      TRY(part_field(c, "xh", P_F64, &x));
+      TRY(part_field(c, "w64", P_F64, &w));
+      TRY(smix(c, c->stream, P_F64, S_G5, x, w, MK_M5T, 1.0, DWF_KC_F64));
+    }
+    TRY(part_hop(ps, P_F64, E_M, "w64", "t64", "", opp, 2, -0.5));
+    TRY(part_hop(ps, P_F64, E_XPAY_G5, "t64", "phi" + std::to_string(sp), "xh", sp, 0, 0.5));
+    TRY(part_hop(ps, P_F64, E_M_XPAY, "phi" + std::to_string(sp), "phi" + std::to_string(opp),
+                 "etap" + std::to_string(opp), opp, 1, 0.5));
+    for (dwf_ctx *c : ps.at)
+      for (int p = 0; p < 2; ++p) {
+        Field ph, psi, t, z;
+        TRY(part_field(c, "phi" + std::to_string(p), P_F64, &ph));
+        TRY(part_field(c, "psi" + std::to_string(p), P_F64, &psi));
+        TRY(smix(c, c->stream, P_F64, S_PLAIN, ph, psi, MK_S2, 1.0, DWF_KC_F64));
+        // D psi of Eq. 5 on both parities: z = ((d - m0)(omega + sigma L) + 1 - L) psi, t = (omega + sigma L) psi
+        TRY(part_field(c, "tt" + std::to_string(p), P_F64, &t));
+        TRY(part_field(c, "z" + std::to_string(p), P_F64, &z));
+        TRY(smix(c, c->stream, P_F64, S_DUAL, psi, t, MK_W, 1.0, DWF_KC_F64, z, MK_Z));
+      }
+    const int *G = c0->pg.G;
+    memset(sol, 0, (size_t)G[0] * G[1] * G[2] * G[3] * c0->Ns * 24 * sizeof(double));
+    for (int p = 0; p < 2; ++p) {
+      TRY(part_gather(ps, "psi" + std::to_string(p), P_F64, p, sol));
+      TRY(part_hop(ps, P_F64, E_XPAY, "tt" + std::to_string(1 - p), "dpsi" + std::to_string(p),
+                   "z" + std::to_string(p), p, 0, -0.5));
+    }
+    double num = 0, den = 0;
+    for (int p = 0; p < 2; ++p) {
+      for (dwf_ctx *c : ps.at) {
+        VecArgs v;
+        memset(&v, 0, sizeof(v));
+        TRY(part_field(c, "eta" + std::to_string(p), P_F64, &v.a));
+        TRY(part_field(c, "dpsi" + std::to_string(p), P_F64, &v.b));
+        v.n = c->h * c->Ns;
+        v.Ns = c->Ns;
+        v.fin = FIN_RED;
+        v.sc = c->d_sc;
+        v.partials = c->d_part;
+        v.ticket = c->d_ticket;
+        CK(diff_norm2_launch(v, c->sm_count, c->stream));
+      }
+      double a = 0, b = 0;
+      TRY(part_sum(ps, 0, &a));
+      TRY(part_norm2(ps, "eta" + std::to_string(p), P_F64, &b));
+      num += a;
+      den += b;
+    }
+    res_full = den > 0 ? sqrt(num / den) : 0.0;
+  } else {
+    const int *G = c0->pg.G;
+    memset(sol, 0, (size_t)G[0] * G[1] * G[2] * G[3] * c0->Ns * 24 * sizeof(double));
+    TRY(part_gather(ps, "xh", P_F64, sp, sol));
+  }
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->iters = iters;
+    stats->restarts = restarts;
+    stats->mode_used = DWF_MODE_RELIABLE;
+    stats->converged = converged ? 1 : 0;
+    stats->true_res = bnorm2 > 0 ? sqrt(rhat2 / bnorm2) : 0.0;
+    stats->true_res_full = res_full;
+    stats->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const double n = (double)c0->pg.G[0] * c0->pg.G[1] * c0->pg.G[2] * c0->pg.G[3] / 2 * c0->Ns;
+    stats->flops = n * (iters * flops_cg_iter(c0->Ns) + restarts * flops_restart(c0->Ns) +
+                        (full ? flops_prep_recon(c0->Ns) : 0.0));
+    stats->inner_prec_used = P;
+  }
+  if (!converged) return fail(c0, DWF_ENOCONV, "max_iter reached");
+  if (full && res_full > prm.tol) return fail(c0, DWF_ENOCONV, "full-system residual above tol");
   return DWF_OK;
 }

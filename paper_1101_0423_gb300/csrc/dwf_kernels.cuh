@@ -859,7 +859,13 @@ struct SmixArgs {
   CGScalars *sc;
   int nrhs;               // batches of right-hand sides as in HopArgs
   size_t fstride, nstride;
+  size_t xfstride;        // bytes between the rows' x (FP32 when the inner fields are 16-bit)
 };
+
+// the inner CG's solution increment x is accumulated in FP32 when the other inner fields
+// are 16-bit: x is never gathered by a hop, and 16-bit rounding of x over a cycle of inner
+// iterations would leave the true residual far above the iterated one
+template <int P> constexpr int x_prec() { return PT<P>::HALF ? P_F32 : P; }
 
 template <int P>
 __host__ __device__ inline size_t smix_smem_bytes(int spb, int Ns, bool dual) {
@@ -908,11 +914,13 @@ __global__ void __launch_bounds__(256) k_smix(const SmixArgs a) {
       }
       load_sp<P>(F(a.p), cb, s, Ns, v);
       {
+        constexpr int PX = x_prec<P>();
+        const Field fx = rb ? field_rhs(a.x, rb, a.xfstride, 0) : a.x;
         R xx[24];
-        load_sp<P>(F(a.x), cb, s, Ns, xx);
+        load_sp<PX>(fx, cb, s, Ns, xx);
 #pragma unroll
         for (int c = 0; c < 24; ++c) xx[c] += alpha * v[c];
-        store_sp<P>(F(a.x), cb, s, Ns, xx);
+        store_sp<PX>(fx, cb, s, Ns, xx);
       }
       R r[24];
       load_sp<P>(F(a.r), cb, s, Ns, r);
@@ -1008,10 +1016,11 @@ __global__ void __launch_bounds__(256) k_accum(const VecArgs v) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < v.n; i += (long)gridDim.x * blockDim.x) {
     const long cb = i / v.Ns;
     const int s = (int)(i % v.Ns);
+    constexpr int PX = x_prec<P>();  // x in FP32 when the inner fields are 16-bit
     double xa[24];
     R xb[24];
     load_sp<P_F64>(v.a, cb, s, v.Ns, xa);
-    load_sp<P>(v.b, cb, s, v.Ns, xb);
+    load_sp<PX>(v.b, cb, s, v.Ns, xb);
     if (v.c.v) {
       R pc[24];
       load_sp<P>(v.c, cb, s, v.Ns, pc);
@@ -1021,7 +1030,7 @@ __global__ void __launch_bounds__(256) k_accum(const VecArgs v) {
 #pragma unroll
     for (int c = 0; c < 24; ++c) { xa[c] += (double)xb[c]; xb[c] = 0; }
     store_sp<P_F64>(v.a, cb, s, v.Ns, xa);
-    store_sp<P>(v.b, cb, s, v.Ns, xb);
+    store_sp<PX>(v.b, cb, s, v.Ns, xb);
   }
 }
 

@@ -143,6 +143,8 @@ def load(build_if_missing: bool = True):
         "dwf_create_part": ([ctypes.POINTER(Partition), i, d, d, dp, dp, ctypes.POINTER(vp)], i),
         "dwf_load_gauge_part": ([vp, dp], i),
         "dwf_part_apply": ([i, ctypes.POINTER(vp), i, i, i, dp, dp], i),
+        "dwf_part_solve": ([i, ctypes.POINTER(vp), dp, dp, ctypes.POINTER(SolveParams),
+                            ctypes.POINTER(SolveStats)], i),
         "dwf_cancel": ([vp, ctypes.c_uint64], i),
         "dwf_server_set_admission": ([vp, i], i),
     }
@@ -376,6 +378,19 @@ def dwf_part_apply(parts, op, prec, parity, x) -> np.ndarray:
     arr = (ctypes.c_void_p * len(parts))(*parts)
     _check(parts[0], load().dwf_part_apply(len(parts), arr, int(op), int(prec), int(parity), _dp(x), _dp(out)))
     return out
+
+
+def dwf_part_solve(parts, rhs, params=None, allow_noconv=False, **kw):
+    """Solve across the parts of a domain decomposition; (global solution, stats dict)."""
+    rhs = _f64(rhs)
+    sol = np.empty_like(rhs)
+    p = _params(params, **kw)
+    st = SolveStats()
+    arr = (ctypes.c_void_p * len(parts))(*parts)
+    rc = load().dwf_part_solve(len(parts), arr, _dp(rhs), _dp(sol), ctypes.byref(p), ctypes.byref(st))
+    if not (allow_noconv and rc == DWF_ENOCONV):
+        _check(parts[0], rc)
+    return sol, st.as_dict()
 
 
 def dwf_last_error(ctx) -> str:
