@@ -39,8 +39,7 @@ PAPER_BEST_GFLOPS = 233.0  # GTX 480, CG (mixed), same lattice (Table 1): other 
 # FP32 kernel classes at this workload, from one ncu capture of the kernels as they stand
 # (summarised under profiles/).  Valid only for the kernel source it was captured on: empty
 # (traffic reported as null) until the kernels are captured again after a change.
-NCU_TRAFFIC = {"hop_m5": 152185344 + 70476544, "hop_xpay": 252870144 + 77556736,
-               "hop_update": 353766144 + 76646656, "smix_p": 302017792 + 238752768}
+NCU_TRAFFIC = {}
 
 
 def flops_ccdag(n, ns):
@@ -555,8 +554,10 @@ def main():
     ap.add_argument("--odwf", action="store_true",
                     help="only the optimal-weights solve on 16^3x32x16 against the cosine weights")
     ap.add_argument("--apply-ccdag", type=int, default=0, metavar="N",
-                    help="only N applications of C C^dagger in FP32 on the benchmark's lattice, inputs and "
+                    help="only N applications of C C^dagger on the benchmark's lattice, inputs and "
                          "launch configuration (a short program for profiler captures)")
+    ap.add_argument("--apply-prec", choices=("f32", "f16", "bf16"), default="f32",
+                    help="arithmetic form of --apply-ccdag")
     ap.add_argument("--configs", action="store_true",
                     help="only the per-configuration table: every workload at its real size, iterations, "
                          "restarts and the oracle-recomputed true residual")
@@ -578,10 +579,12 @@ def main():
         y = torch.empty_like(x)
         with dwf.Context(DIMS, NS, M0, MQ, om, sg, inputs.gauge_field(DIMS, EPS, seed=SEED)) as ctx:
             stream = torch.cuda.current_stream()
+            prec = {"f32": dwf.PREC_F32, "f16": dwf.PREC_F16, "bf16": dwf.PREC_BF16}[args.apply_prec]
             for _ in range(args.apply_ccdag):
-                dwf.dwf_apply_eo_dev(ctx.h, dwf.OP_CCDAG, dwf.PREC_F32, 1, x, y, stream=stream)
+                dwf.dwf_apply_eo_dev(ctx.h, dwf.OP_CCDAG, prec, 1, x, y, stream=stream)
             stream.synchronize()
-        print(json.dumps({"applied": "C C^dagger FP32", "times": args.apply_ccdag, "max_abs": float(y.abs().max())}))
+        print(json.dumps({"applied": "C C^dagger " + args.apply_prec, "times": args.apply_ccdag,
+                          "max_abs": float(y.abs().max())}))
         return
     if args.configs:
         from paper_1101_0423_gb300 import build as _b

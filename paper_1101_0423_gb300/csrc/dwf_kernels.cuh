@@ -487,8 +487,11 @@ __global__ void __launch_bounds__(256) k_hop(const HopArgs a) {
         const SignPairs fw = sign_pairs(-1.f), bw = sign_pairs(1.f);
         const float4 *myW =
             (SM::EXPAND ? sP : reinterpret_cast<const float4 *>(sL)) + (size_t)sl * LINK_SITE_F4;
+        // the forward and backward hops of one direction in turn: both gather from the same
+        // rows of the input for mu = x, so the second finds most of its lines in L1
 #pragma unroll
-        for (int d = 0; d < 8; ++d) {
+        for (int dd = 0; dd < 8; ++dd) {
+          const int d = (dd >> 1) + 4 * (dd & 1);
           float ps1[24];
           load_sp_ro<P>(F(a.in), nb[d], s, Ns, ps1);
           f2 ps[12];
