@@ -39,7 +39,8 @@ PAPER_BEST_GFLOPS = 233.0  # GTX 480, CG (mixed), same lattice (Table 1): other 
 # FP32 kernel classes at this workload, from one ncu capture of the kernels as they stand
 # (summarised under profiles/).  Valid only for the kernel source it was captured on: empty
 # (traffic reported as null) until the kernels are captured again after a change.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"hop_m5": 152075008 + 70445312, "hop_xpay": 252933120 + 74510848,
+               "hop_update": 353506304 + 76856064, "smix_p": 302014976 + 238914816}
 
 
 def flops_ccdag(n, ns):
