@@ -219,6 +219,25 @@ dwf_status dwf_solve_batch(dwf_ctx *ctx, int nrhs, const double *rhs, double *so
 dwf_status dwf_solve_batch_dev(dwf_ctx *ctx, int nrhs, const double *d_rhs, double *d_sol,
                                const dwf_solve_params *params, dwf_solve_stats *stats, void *stream);
 
+/* Solve a ragged set: one system on each of n distinct contexts of one device, which may
+ * differ in lattice, Ns, masses and weights (e.g. one gauge field shared by handle, eight
+ * (Ns, mq) pairs), with the same params (use_x0 not allowed).  rhs[k] and sol[k] are
+ * arrays of the dwf_solve layout of context k; stats, if not NULL, receives n entries, each
+ * time_ms spanning that system's own begin and end.  Every system follows Algorithm 1-2 with
+ * its own scalars, restarts and convergence (Sec. 2.3), and the same kernels as it would
+ * alone, so each solution equals its single solve bit for bit; each interval of check_every
+ * inner iterations of all unfinished systems is one CUDA graph with a branch per context, so
+ * the systems' kernels run concurrently, and the restarts between intervals run on each
+ * context's own stream.  Errors about the set as a whole (duplicate contexts, contexts on
+ * different devices) are reported on ctxs[0]; those of one system on its context.  Returns
+ * the first failure (DWF_ENOCONV if any system did not converge).  n: 1..256. */
+dwf_status dwf_solve_ragged(int n, dwf_ctx *const *ctxs, const double *const *rhs, double *const *sol,
+                            const dwf_solve_params *params, dwf_solve_stats *stats);
+/* Same with caller-owned device arrays; the set starts after, and `stream` continues after
+ * it (NULL: ctxs[0]'s stream). */
+dwf_status dwf_solve_ragged_dev(int n, dwf_ctx *const *ctxs, const double *const *d_rhs, double *const *d_sol,
+                                const dwf_solve_params *params, dwf_solve_stats *stats, void *stream);
+
 /* Quark propagator from the point x0 (the valence use of Sec. 2.2): the 12 spin-colour
  * point sources are solved in one batch (dwf_solve_batch, DWF_SYS_FULL) and the 4D quark
  * field is read off the two walls.  Conventions (the paper fixes none): source (beta, b)

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <chrono>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -1448,35 +1449,57 @@ struct RhsState {
   dwf_status status = DWF_OK;
 };
 
-// Solve K systems with the same operator; rhs/sol hold K full-lattice arrays one after another.
-dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf_solve_params prm,
-                      dwf_solve_stats *S_out, cudaStream_t st) {
-  const double delta = prm.delta > 0.0 ? prm.delta : 0.01;
-  const bool full = prm.system == DWF_SYS_FULL;
-  const int stall_iters = prm.stall_iters > 0 ? prm.stall_iters : 500;
-  const char *trace_env = getenv("DWF_TRACE");
-  const bool trace = trace_env && trace_env[0] == '1';
-  for (int k = 0; k < K; ++k) memset(&S_out[k], 0, sizeof(dwf_solve_stats));
-  begin_profile(c, prm.profile != 0);
-  const long long launches0 = c->launches;
-  TRY(ensure_gauge(c, P_F64, st));
-  TRY(ensure_gauge(c, prm.inner_prec, st));
-  cudaEvent_t ev0 = next_event(c), ev1 = next_event(c);
-  CK(cudaEventRecord(ev0, st));
+// One solve of K systems with the same operator (rhs/sol hold K full-lattice arrays one after
+// another), taken in steps by its driver: begin() forms the sources and arms the inner CG;
+// while !all_done(), one interval of check_every inner iterations is enqueued
+// (enqueue_interval keeps this run's own CUDA graph; record_interval only enqueues, for a
+// driver that captures several runs into one graph), the batch scalars are read back
+// (fetch_scalars) and process_interval() takes the FP64 restarts that fell due; then
+// after_loop() reconstructs the solutions (and re-arms the systems that need a tightened
+// pass) and finish() fills the stats.  solve_core drives one run; dwf_solve_ragged drives
+// one per context, with the intervals of all of them in one graph.
+struct SolveRun {
+  dwf_ctx *c;
+  int K;
+  const double *d_rhs;
+  double *d_sol;
+  dwf_solve_params prm;
+  dwf_solve_stats *S_out;
+  cudaStream_t st;
 
+  double delta = 0.01;
+  bool full = false;
+  int stall_iters = 500;
+  bool trace = false;
+  long long launches0 = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   SolveState S;
-  S.prec = prm.inner_prec;
-  S.sp = prm.schur_parity;
-  S.op = 1 - S.sp;
-  S.K = K;
-  TRY(get_buf_k(c, "b", P_F64, K, &S.b));
-  TRY(get_buf_k(c, "xh", P_F64, K, &S.xh));
-  TRY(get_buf_k(c, "rh", P_F64, K, &S.rh));
-  TRY(get_buf(c, "w64", P_F64, &S.w64));
-  TRY(get_buf(c, "t64", P_F64, &S.t64));
-  TRY(get_buf(c, "q64", P_F64, &S.q64));
-  TRY(get_buf(c, "u64", P_F64, &S.u64));
-  auto inner_bufs = [&]() -> dwf_status {
+  Field eta[2], etap[2], phi[2], psi[2], dpsi[2];
+  Slots sl;
+  Geom g;
+  size_t full_doubles = 0, nbytes64 = 0;
+  double tol_schur = 0;
+  std::vector<RhsState> R;
+  int escalations = 0;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  bool use_graph = false;
+  bool first_batch = true;
+  bool graph_dirty = false;  // a record_interval capture of this run is out of date
+  int pass = 0;              // after_loop calls so far
+  std::vector<int> again;    // systems of the tightened pass
+  bool tuned_saved = false, prev_tuned = true;
+
+  SolveRun(dwf_ctx *c_, int K_, const double *rhs, double *sol, const dwf_solve_params &p, dwf_solve_stats *out,
+           cudaStream_t s)
+      : c(c_), K(K_), d_rhs(rhs), d_sol(sol), prm(p), S_out(out), st(s) {}
+  ~SolveRun() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (tuned_saved) c->use_tuned = prev_tuned;  // the solve's own choice, not the context's
+  }
+
+  dwf_status inner_bufs() {
     TRY(get_buf_k(c, "cg_x", xprec(S.prec), K, &S.x));
     TRY(get_buf_k(c, "cg_r", S.prec, K, &S.r));
     TRY(get_buf_k(c, "cg_p", S.prec, K, &S.p));
@@ -1485,38 +1508,10 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
     TRY(get_buf_k(c, "cg_t", S.prec, K, &S.t));
     TRY(get_buf_k(c, "cg_u", S.prec, K, &S.u));
     return DWF_OK;
-  };
-  TRY(inner_bufs());
-  struct TunedScope {  // the solve's own choice, restored for the context's later calls
-    dwf_ctx *c;
-    bool prev;
-    ~TunedScope() { c->use_tuned = prev; }
-  } tuned_scope{c, c->use_tuned};
-  c->use_tuned = !prm.no_autotune;
-  if (!prm.no_autotune) TRY(tune_inner(c, st, S));
-  Field eta[2], etap[2], phi[2], psi[2], dpsi[2];
-  if (full)
-    for (int p = 0; p < 2; ++p) {
-      TRY(get_buf(c, "eta" + std::to_string(p), P_F64, &eta[p]));
-      TRY(get_buf(c, "etap" + std::to_string(p), P_F64, &etap[p]));
-      TRY(get_buf(c, "phi" + std::to_string(p), P_F64, &phi[p]));
-      TRY(get_buf(c, "psi" + std::to_string(p), P_F64, &psi[p]));
-      TRY(get_buf(c, "dpsi" + std::to_string(p), P_F64, &dpsi[p]));
-    }
-  Slots sl;
-  TRY(batch_slots(c, K, &sl));
-  const Geom g = geom(c);
-  const size_t full_doubles = (size_t)c->V4 * c->Ns * 24;
-  const size_t nbytes64 = field_bytes(c, P_F64);
-  // the full-system residual runs a little above the Schur one (by at most cond(S1)): the
-  // Schur system of a full solve aims at schur_target_pct of the tolerance (default 50 %),
-  // and the systems that still miss it take one tightened pass below
-  const double tol_schur = full ? 0.01 * (prm.schur_target_pct > 0 ? prm.schur_target_pct : 50) * prm.tol : prm.tol;
-  std::vector<RhsState> R(K);
-  int escalations = 0;
+  }
 
   // eta'_k = S1 eta_k on both parities (the shared temporaries eta, etap)
-  auto prep_eta = [&](int k) -> dwf_status {
+  dwf_status prep_eta(int k) {
     for (int p = 0; p < 2; ++p) {
       {
         Timed t(c, st, DWF_KC_F64);
@@ -1525,12 +1520,12 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
       TRY(smix(c, st, P_F64, S_PLAIN, eta[p], etap[p], MK_S1, 1.0, DWF_KC_F64));
     }
     return DWF_OK;
-  };
+  }
 
   // (re)arm the inner CG of right-hand side k after a restart: r_k holds r_hat in the inner
   // precision with |r|^2 = rr_conv.  Reliable updates keep p (beta from the recomputed
   // residual), defect correction restarts from p = r (beta = 0).
-  auto arm = [&](int k, double tol_now, bool first, bool reset_p, double rr_conv) -> dwf_status {
+  dwf_status arm(int k, double tol_now, bool first, bool reset_p, double rr_conv) {
     UseSlot use(c, sl, k);
     CGScalars &h = *c->h_sc;
     if (first) {
@@ -1556,158 +1551,210 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
     h.target2 = tol_now * tol_now * R[k].bnorm2;
     h.restart_flag = R[k].done ? RS_DONE : 0;
     return push_scalars(c, st);
-  };
-
-  // ---- source: b_k on the Schur parity (Eq. 10 for the full system); x_hat = 0, r_hat = b,
-  // r = b in the inner precision, x = p = 0
-  CK(cudaMemsetAsync(S.x.v, 0, (size_t)K * field_bytes(c, xprec(S.prec)), st));
-  CK(cudaMemsetAsync(S.p.v, 0, (size_t)K * field_bytes(c, S.prec), st));
-  if (S.p.nrm) CK(cudaMemsetAsync(S.p.nrm, 0, (size_t)K * c->h * c->Ns * sizeof(float), st));
-  CK(cudaMemsetAsync(S.xh.v, 0, (size_t)K * nbytes64, st));
-  for (int k = 0; k < K; ++k) {
-    UseSlot use(c, sl, k);
-    const Field bk = at(c, S.b, k, P_F64);
-    if (full) {
-      TRY(prep_eta(k));
-      // b = eta'_sp - M5 D^{sp,op} eta'_op = eta'_sp + 1/2 M5 H eta'_op
-      HopArgs a = hop_args(c, P_F64, S.sp);
-      a.in = etap[S.op];
-      a.y = etap[S.sp];
-      a.out = bk;
-      set_m5(a, c, P_F64, false);
-      a.coef = 0.5;
-      TRY(hop(c, st, P_F64, E_M_XPAY, a, DWF_KC_F64));
-    } else {
-      Timed t(c, st, DWF_KC_F64);
-      CK(pack_any(P_F64, d_rhs + (size_t)k * full_doubles, bk, g, S.sp, c->sm_count, st));
-    }
-    TRY(norm2(c, st, P_F64, bk, FIN_RED));
-    CK(cudaMemcpyAsync(at(c, S.rh, k, P_F64).v, bk.v, nbytes64, cudaMemcpyDeviceToDevice, st));
-    TRY(convert(c, st, P_F64, bk, S.prec, at(c, S.r, k, S.prec), DWF_KC_OTHER));
-    TRY(norm2(c, st, S.prec, at(c, S.r, k, S.prec), FIN_RED2));
-    TRY(pull_scalars(c, st));
-    R[k].bnorm2 = R[k].rhat2 = R[k].prev_rhat2 = c->h_sc->red;
-    R[k].rr_last = c->h_sc->red2;
-    R[k].mode = prm.mode == DWF_MODE_DEFECT ? DWF_MODE_DEFECT : DWF_MODE_RELIABLE;
-    R[k].done = R[k].converged = R[k].bnorm2 == 0.0;
-  }
-  for (int k = 0; k < K; ++k) {
-    R[k].tol = tol_schur;
-    TRY(arm(k, tol_schur, true, true, R[k].rr_last));
   }
 
-  cudaGraphExec_t gexec = nullptr;
-  cudaGraph_t graph = nullptr;
-  struct GraphGuard {
-    cudaGraphExec_t &e;
-    cudaGraph_t &gr;
-    ~GraphGuard() {
-      if (e) cudaGraphExecDestroy(e);
-      if (gr) cudaGraphDestroy(gr);
+  dwf_status begin() {
+    delta = prm.delta > 0.0 ? prm.delta : 0.01;
+    full = prm.system == DWF_SYS_FULL;
+    stall_iters = prm.stall_iters > 0 ? prm.stall_iters : 500;
+    const char *trace_env = getenv("DWF_TRACE");
+    trace = trace_env && trace_env[0] == '1';
+    for (int k = 0; k < K; ++k) memset(&S_out[k], 0, sizeof(dwf_solve_stats));
+    begin_profile(c, prm.profile != 0);
+    launches0 = c->launches;
+    TRY(ensure_gauge(c, P_F64, st));
+    TRY(ensure_gauge(c, prm.inner_prec, st));
+    ev0 = next_event(c);
+    ev1 = next_event(c);
+    CK(cudaEventRecord(ev0, st));
+
+    S.prec = prm.inner_prec;
+    S.sp = prm.schur_parity;
+    S.op = 1 - S.sp;
+    S.K = K;
+    TRY(get_buf_k(c, "b", P_F64, K, &S.b));
+    TRY(get_buf_k(c, "xh", P_F64, K, &S.xh));
+    TRY(get_buf_k(c, "rh", P_F64, K, &S.rh));
+    TRY(get_buf(c, "w64", P_F64, &S.w64));
+    TRY(get_buf(c, "t64", P_F64, &S.t64));
+    TRY(get_buf(c, "q64", P_F64, &S.q64));
+    TRY(get_buf(c, "u64", P_F64, &S.u64));
+    TRY(inner_bufs());
+    prev_tuned = c->use_tuned;
+    tuned_saved = true;
+    c->use_tuned = !prm.no_autotune;
+    if (!prm.no_autotune) TRY(tune_inner(c, st, S));
+    if (full)
+      for (int p = 0; p < 2; ++p) {
+        TRY(get_buf(c, "eta" + std::to_string(p), P_F64, &eta[p]));
+        TRY(get_buf(c, "etap" + std::to_string(p), P_F64, &etap[p]));
+        TRY(get_buf(c, "phi" + std::to_string(p), P_F64, &phi[p]));
+        TRY(get_buf(c, "psi" + std::to_string(p), P_F64, &psi[p]));
+        TRY(get_buf(c, "dpsi" + std::to_string(p), P_F64, &dpsi[p]));
+      }
+    TRY(batch_slots(c, K, &sl));
+    g = geom(c);
+    full_doubles = (size_t)c->V4 * c->Ns * 24;
+    nbytes64 = field_bytes(c, P_F64);
+    // the full-system residual runs a little above the Schur one (by at most cond(S1)): the
+    // Schur system of a full solve aims at schur_target_pct of the tolerance (default 50 %),
+    // and the systems that still miss it take one tightened pass below
+    tol_schur = full ? 0.01 * (prm.schur_target_pct > 0 ? prm.schur_target_pct : 50) * prm.tol : prm.tol;
+    R.assign(K, RhsState());
+
+    // ---- source: b_k on the Schur parity (Eq. 10 for the full system); x_hat = 0, r_hat = b,
+    // r = b in the inner precision, x = p = 0
+    CK(cudaMemsetAsync(S.x.v, 0, (size_t)K * field_bytes(c, xprec(S.prec)), st));
+    CK(cudaMemsetAsync(S.p.v, 0, (size_t)K * field_bytes(c, S.prec), st));
+    if (S.p.nrm) CK(cudaMemsetAsync(S.p.nrm, 0, (size_t)K * c->h * c->Ns * sizeof(float), st));
+    CK(cudaMemsetAsync(S.xh.v, 0, (size_t)K * nbytes64, st));
+    for (int k = 0; k < K; ++k) {
+      UseSlot use(c, sl, k);
+      const Field bk = at(c, S.b, k, P_F64);
+      if (full) {
+        TRY(prep_eta(k));
+        // b = eta'_sp - M5 D^{sp,op} eta'_op = eta'_sp + 1/2 M5 H eta'_op
+        HopArgs a = hop_args(c, P_F64, S.sp);
+        a.in = etap[S.op];
+        a.y = etap[S.sp];
+        a.out = bk;
+        set_m5(a, c, P_F64, false);
+        a.coef = 0.5;
+        TRY(hop(c, st, P_F64, E_M_XPAY, a, DWF_KC_F64));
+      } else {
+        Timed t(c, st, DWF_KC_F64);
+        CK(pack_any(P_F64, d_rhs + (size_t)k * full_doubles, bk, g, S.sp, c->sm_count, st));
+      }
+      TRY(norm2(c, st, P_F64, bk, FIN_RED));
+      CK(cudaMemcpyAsync(at(c, S.rh, k, P_F64).v, bk.v, nbytes64, cudaMemcpyDeviceToDevice, st));
+      TRY(convert(c, st, P_F64, bk, S.prec, at(c, S.r, k, S.prec), DWF_KC_OTHER));
+      TRY(norm2(c, st, S.prec, at(c, S.r, k, S.prec), FIN_RED2));
+      TRY(pull_scalars(c, st));
+      R[k].bnorm2 = R[k].rhat2 = R[k].prev_rhat2 = c->h_sc->red;
+      R[k].rr_last = c->h_sc->red2;
+      R[k].mode = prm.mode == DWF_MODE_DEFECT ? DWF_MODE_DEFECT : DWF_MODE_RELIABLE;
+      R[k].done = R[k].converged = R[k].bnorm2 == 0.0;
     }
-  } graph_guard{gexec, graph};
-  const bool use_graph = prm.use_graph && !c->profiling;
-  bool first_batch = true;
-  auto all_done = [&]() {
+    for (int k = 0; k < K; ++k) {
+      R[k].tol = tol_schur;
+      TRY(arm(k, tol_schur, true, true, R[k].rr_last));
+    }
+    use_graph = prm.use_graph && !c->profiling;
+    first_batch = true;
+    return DWF_OK;
+  }
+
+  bool all_done() const {
     for (auto &x : R)
       if (!x.done) return false;
     return true;
-  };
+  }
 
-  // ---- mixed-precision CG until every |b_k - A x_hat_k| <= R[k].tol |b_k| (FP64)
-  auto cg_loop = [&]() -> dwf_status {
-    while (!all_done()) {
-      // one batch of inner iterations (the device skips a right-hand side once its restart
-      // is due or it is finished)
-      if (use_graph && !first_batch) {
-        if (!gexec) {
-          CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-          const long long l0 = c->launches;
-          for (int it = 0; it < prm.check_every; ++it) {
-            dwf_status s2 = cg_iteration(c, st, S, sl);
-            if (s2 != DWF_OK) {
-              cudaStreamEndCapture(st, &graph);
-              return s2;
-            }
-          }
-          c->launches = l0;
-          CK(cudaStreamEndCapture(st, &graph));
-          CK(cudaGraphInstantiate(&gexec, graph, 0));
+  // one interval of inner iterations, enqueued on s (the device skips a right-hand side
+  // once its restart is due or it is finished)
+  dwf_status record_interval(cudaStream_t s) {
+    for (int it = 0; it < prm.check_every; ++it) TRY(cg_iteration(c, s, S, sl));
+    return DWF_OK;
+  }
+
+  // the same on st, replayed from this run's own graph after the first interval
+  dwf_status enqueue_interval() {
+    if (use_graph && !first_batch) {
+      if (!gexec) {
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const long long l0 = c->launches;
+        dwf_status s2 = record_interval(st);
+        if (s2 != DWF_OK) {
+          cudaStreamEndCapture(st, &graph);
+          return s2;
         }
-        CK(cudaGraphLaunch(gexec, st));
-        c->launches += 5LL * prm.check_every;
-      } else {
-        for (int it = 0; it < prm.check_every; ++it) TRY(cg_iteration(c, st, S, sl));
+        c->launches = l0;
+        CK(cudaStreamEndCapture(st, &graph));
+        CK(cudaGraphInstantiate(&gexec, graph, 0));
       }
-      first_batch = false;
-      CK(cudaMemcpyAsync(sl.h_sc, sl.d_sc, K * sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      for (int k = 0; k < K; ++k) {
-        if (R[k].done) continue;
-        UseSlot use(c, sl, k);
-        if (c->h_sc->error) TRY(pull_scalars(c, st));  // reports DWF_ETIMEOUT and resets
-        const int reason = c->h_sc->restart_flag;
-        if (!reason) continue;
-        R[k].iters = c->h_sc->iter;
-        // ---- reliable update / defect correction restart in FP64
-        TRY(fp64_restart(c, st, S, k));
+      CK(cudaGraphLaunch(gexec, st));
+      c->launches += 5LL * prm.check_every;
+    } else {
+      TRY(record_interval(st));
+    }
+    first_batch = false;
+    return DWF_OK;
+  }
+
+  // the batch scalars to the host, after the work enqueued on s
+  dwf_status fetch_scalars(cudaStream_t s) {
+    CK(cudaMemcpyAsync(sl.h_sc, sl.d_sc, K * sizeof(CGScalars), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return DWF_OK;
+  }
+
+  // ---- after an interval: the FP64 restarts that fell due (reliable update / defect
+  // correction), convergence to |b_k - A x_hat_k| <= R[k].tol |b_k| (FP64)
+  dwf_status process_interval() {
+    for (int k = 0; k < K; ++k) {
+      if (R[k].done) continue;
+      UseSlot use(c, sl, k);
+      if (c->h_sc->error) TRY(pull_scalars(c, st));  // reports DWF_ETIMEOUT and resets
+      const int reason = c->h_sc->restart_flag;
+      if (!reason) continue;
+      R[k].iters = c->h_sc->iter;
+      TRY(fp64_restart(c, st, S, k));
+      TRY(pull_scalars(c, st));
+      ++R[k].restarts;
+      R[k].rhat2 = c->h_sc->red;
+      R[k].rr_last = c->h_sc->red2;
+      if (trace)
+        fprintf(stderr, "dwf: rhs %d restart %d iter %d reason %d |r_iter|/|b| %.3e |r_true|/|b| %.3e mode %s\n", k,
+                R[k].restarts, R[k].iters, reason, sqrt(c->h_sc->rr / R[k].bnorm2), sqrt(R[k].rhat2 / R[k].bnorm2),
+                R[k].mode == DWF_MODE_DEFECT ? "defect" : "reliable");
+      const double tol_now = R[k].tol;
+      if (!std::isfinite(R[k].rhat2)) {
+        R[k].done = true;
+        R[k].status = fail(c, DWF_ENOCONV, "residual is not finite");
+      } else if (R[k].rhat2 <= tol_now * tol_now * R[k].bnorm2) {
+        R[k].done = R[k].converged = true;
+      } else if (R[k].iters >= prm.max_iter) {
+        R[k].done = true;
+        R[k].status = fail(c, DWF_ENOCONV, "max_iter reached");
+      }
+      if (R[k].done) {
+        TRY(arm(k, tol_now, false, true, R[k].rr_last));  // parks the right-hand side
+        continue;
+      }
+      // Sec. 2.3: fall back to defect correction when the reliable updates stop converging
+      // (the true residual grew, or the inner recursion diverged or stalled)
+      const bool failed = R[k].rhat2 > R[k].prev_rhat2 || reason == RS_DIVERGED || reason == RS_STALLED;
+      if (prm.mode == DWF_MODE_AUTO && R[k].mode == DWF_MODE_RELIABLE && failed) {
+        R[k].mode = DWF_MODE_DEFECT;
+      } else if (prm.mode == DWF_MODE_AUTO && R[k].mode == DWF_MODE_DEFECT && failed && S.prec >= P_F16 && K == 1) {
+        // 16-bit storage is too coarse for this system: continue from x_hat with FP32
+        // inner iterations (the FP64 state x_hat, r_hat is untouched)
+        TRY(ensure_gauge(c, P_F32, st));
+        S.prec = P_F32;
+        TRY(inner_bufs());
+        CK(cudaMemsetAsync(S.x.v, 0, field_bytes(c, xprec(S.prec)), st));
+        CK(cudaMemsetAsync(S.p.v, 0, field_bytes(c, S.prec), st));
+        TRY(convert(c, st, P_F64, S.rh, S.prec, S.r, DWF_KC_F64));
+        TRY(norm2(c, st, S.prec, S.r, FIN_RED2));
         TRY(pull_scalars(c, st));
-        ++R[k].restarts;
-        R[k].rhat2 = c->h_sc->red;
         R[k].rr_last = c->h_sc->red2;
-        if (trace)
-          fprintf(stderr, "dwf: rhs %d restart %d iter %d reason %d |r_iter|/|b| %.3e |r_true|/|b| %.3e mode %s\n", k,
-                  R[k].restarts, R[k].iters, reason, sqrt(c->h_sc->rr / R[k].bnorm2), sqrt(R[k].rhat2 / R[k].bnorm2),
-                  R[k].mode == DWF_MODE_DEFECT ? "defect" : "reliable");
-        const double tol_now = R[k].tol;
-        if (!std::isfinite(R[k].rhat2)) {
-          R[k].done = true;
-          R[k].status = fail(c, DWF_ENOCONV, "residual is not finite");
-        } else if (R[k].rhat2 <= tol_now * tol_now * R[k].bnorm2) {
-          R[k].done = R[k].converged = true;
-        } else if (R[k].iters >= prm.max_iter) {
-          R[k].done = true;
-          R[k].status = fail(c, DWF_ENOCONV, "max_iter reached");
-        }
-        if (R[k].done) {
-          TRY(arm(k, tol_now, false, true, R[k].rr_last));  // parks the right-hand side
-          continue;
-        }
-        // Sec. 2.3: fall back to defect correction when the reliable updates stop converging
-        // (the true residual grew, or the inner recursion diverged or stalled)
-        const bool failed = R[k].rhat2 > R[k].prev_rhat2 || reason == RS_DIVERGED || reason == RS_STALLED;
-        if (prm.mode == DWF_MODE_AUTO && R[k].mode == DWF_MODE_RELIABLE && failed) {
-          R[k].mode = DWF_MODE_DEFECT;
-        } else if (prm.mode == DWF_MODE_AUTO && R[k].mode == DWF_MODE_DEFECT && failed && S.prec >= P_F16 &&
-                   K == 1) {
-          // 16-bit storage is too coarse for this system: continue from x_hat with FP32
-          // inner iterations (the FP64 state x_hat, r_hat is untouched)
-          TRY(ensure_gauge(c, P_F32, st));
-          S.prec = P_F32;
-          TRY(inner_bufs());
-          CK(cudaMemsetAsync(S.x.v, 0, field_bytes(c, xprec(S.prec)), st));
-          CK(cudaMemsetAsync(S.p.v, 0, field_bytes(c, S.prec), st));
-          TRY(convert(c, st, P_F64, S.rh, S.prec, S.r, DWF_KC_F64));
-          TRY(norm2(c, st, S.prec, S.r, FIN_RED2));
-          TRY(pull_scalars(c, st));
-          R[k].rr_last = c->h_sc->red2;
-          if (gexec) cudaGraphExecDestroy(gexec);
-          if (graph) cudaGraphDestroy(graph);
-          gexec = nullptr;
-          graph = nullptr;
-          first_batch = true;
-          ++escalations;
-        }
-        R[k].prev_rhat2 = R[k].rhat2;
-        TRY(arm(k, tol_now, false, R[k].mode == DWF_MODE_DEFECT || failed, R[k].rr_last));
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+        first_batch = true;
+        graph_dirty = true;
+        ++escalations;
       }
+      R[k].prev_rhat2 = R[k].rhat2;
+      TRY(arm(k, tol_now, false, R[k].mode == DWF_MODE_DEFECT || failed, R[k].rr_last));
     }
     return DWF_OK;
-  };
+  }
 
   // ---- solution k: phi_sp = C^dag x_hat; phi_op = eta'_op - M5 D^{op,sp} phi_sp; psi = S2 phi,
   // unpacked to sol_k; then |eta - D psi| / |eta| in FP64
-  auto reconstruct = [&](int k) -> dwf_status {
+  dwf_status reconstruct(int k) {
     UseSlot use(c, sl, k);
     TRY(prep_eta(k));
     TRY(op_cdag(c, st, P_F64, S.sp, at(c, S.xh, k, P_F64), phi[S.sp], S.w64, S.t64, DWF_KC_F64));
@@ -1747,69 +1794,101 @@ dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf
     }
     R[k].res_full = den > 0 ? sqrt(num / den) : 0.0;
     return DWF_OK;
-  };
+  }
 
-  dwf_status loop_st = cg_loop();
-  if (loop_st != DWF_OK && loop_st != DWF_ENOCONV) return loop_st;
-  if (full) {
-    for (int k = 0; k < K; ++k) TRY(reconstruct(k));
-    // a system whose full residual still misses the target continues from x_hat with its
-    // Schur tolerance tightened once (each row of a batch as it would alone; the others
-    // stay parked)
-    std::vector<int> again;
-    for (int k = 0; k < K; ++k)
-      if (R[k].converged && R[k].res_full > prm.tol) again.push_back(k);
-    if (!again.empty()) {
-      for (int k : again) {
-        R[k].tol = tol_schur * std::min(0.1, 0.5 * prm.tol / R[k].res_full);
-        R[k].done = R[k].converged = false;
-        TRY(arm(k, R[k].tol, false, R[k].mode == DWF_MODE_DEFECT, R[k].rr_last));
+  // after the inner loop has finished every system: the solutions (full system: each
+  // reconstructed and its full residual taken; a system whose full residual still misses
+  // the target continues from x_hat with its Schur tolerance tightened once, each row of a
+  // batch as it would alone, the others parked).  *more: the tightened pass is armed and the
+  // loop has to run again before the next call.
+  dwf_status after_loop(bool *more) {
+    *more = false;
+    if (full) {
+      if (pass == 0) {
+        for (int k = 0; k < K; ++k) TRY(reconstruct(k));
+        for (int k = 0; k < K; ++k)
+          if (R[k].converged && R[k].res_full > prm.tol) again.push_back(k);
+        for (int k : again) {
+          R[k].tol = tol_schur * std::min(0.1, 0.5 * prm.tol / R[k].res_full);
+          R[k].done = R[k].converged = false;
+          TRY(arm(k, R[k].tol, false, R[k].mode == DWF_MODE_DEFECT, R[k].rr_last));
+        }
+        *more = !again.empty();
+      } else {
+        for (int k : again) TRY(reconstruct(k));
       }
-      loop_st = cg_loop();
-      if (loop_st != DWF_OK && loop_st != DWF_ENOCONV) return loop_st;
-      for (int k : again) TRY(reconstruct(k));
+    } else {
+      CK(cudaMemsetAsync(d_sol, 0, (size_t)K * full_doubles * sizeof(double), st));
+      for (int k = 0; k < K; ++k) {
+        Timed t(c, st, DWF_KC_F64);
+        CK(unpack_any(P_F64, at(c, S.xh, k, P_F64), d_sol + (size_t)k * full_doubles, g, S.sp, c->sm_count, st));
+      }
     }
-  } else {
-    CK(cudaMemsetAsync(d_sol, 0, (size_t)K * full_doubles * sizeof(double), st));
+    ++pass;
+    return DWF_OK;
+  }
+
+  dwf_status finish() {
+    CK(cudaEventRecord(ev1, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpyAsync(sl.h_sc, sl.d_sc, K * sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    const double n = (double)c->h * c->Ns;
+    end_profile(c, &S_out[0]);
+    dwf_status result = DWF_OK;
     for (int k = 0; k < K; ++k) {
-      Timed t(c, st, DWF_KC_F64);
-      CK(unpack_any(P_F64, at(c, S.xh, k, P_F64), d_sol + (size_t)k * full_doubles, g, S.sp, c->sm_count, st));
+      dwf_solve_stats &o = S_out[k];
+      if (k > 0) {
+        memcpy(o.class_ms, S_out[0].class_ms, sizeof(o.class_ms));
+        memcpy(o.class_launches, S_out[0].class_launches, sizeof(o.class_launches));
+      }
+      o.iters = sl.h_sc[k].iter;
+      o.restarts = R[k].restarts;
+      o.mode_used = R[k].mode;
+      o.converged = R[k].converged ? 1 : 0;
+      o.true_res = R[k].bnorm2 > 0 ? sqrt(R[k].rhat2 / R[k].bnorm2) : 0.0;
+      o.true_res_full = full ? R[k].res_full : 0.0;
+      o.flops = n * (o.iters * flops_cg_iter(c->Ns) + o.restarts * flops_restart(c->Ns) +
+                     (full ? flops_prep_recon(c->Ns) : 0.0));
+      o.time_ms = ms;
+      // algorithmic bytes: 18 (16-bit: 12) reals per link, whatever padding the layout adds
+      const double lb = S.prec == P_F64 ? 144.0 : S.prec == P_F32 ? 72.0 : 24.0;
+      o.bytes_hop_m5 = n * (2.0 * site_bytes(S.prec) + 8.0 * lb / c->Ns);
+      o.inner_prec_used = S.prec;
+      o.escalations = escalations;
+      o.kernel_launches = c->launches - launches0;
+      if (R[k].status != DWF_OK && result == DWF_OK) result = R[k].status;
+      if (!R[k].converged && result == DWF_OK) result = fail(c, DWF_ENOCONV, "not converged");
     }
+    return result;
   }
-  CK(cudaEventRecord(ev1, st));
-  CK(cudaStreamSynchronize(st));
-  CK(cudaMemcpyAsync(sl.h_sc, sl.d_sc, K * sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  float ms = 0;
-  cudaEventElapsedTime(&ms, ev0, ev1);
-  const double n = (double)c->h * c->Ns;
-  end_profile(c, &S_out[0]);
-  dwf_status result = DWF_OK;
-  for (int k = 0; k < K; ++k) {
-    dwf_solve_stats &o = S_out[k];
-    if (k > 0) {
-      memcpy(o.class_ms, S_out[0].class_ms, sizeof(o.class_ms));
-      memcpy(o.class_launches, S_out[0].class_launches, sizeof(o.class_launches));
-    }
-    o.iters = sl.h_sc[k].iter;
-    o.restarts = R[k].restarts;
-    o.mode_used = R[k].mode;
-    o.converged = R[k].converged ? 1 : 0;
-    o.true_res = R[k].bnorm2 > 0 ? sqrt(R[k].rhat2 / R[k].bnorm2) : 0.0;
-    o.true_res_full = full ? R[k].res_full : 0.0;
-    o.flops = n * (o.iters * flops_cg_iter(c->Ns) + o.restarts * flops_restart(c->Ns) +
-                   (full ? flops_prep_recon(c->Ns) : 0.0));
-    o.time_ms = ms;
-    // algorithmic bytes: 18 (16-bit: 12) reals per link, whatever padding the layout adds
-    const double lb = S.prec == P_F64 ? 144.0 : S.prec == P_F32 ? 72.0 : 24.0;
-    o.bytes_hop_m5 = n * (2.0 * site_bytes(S.prec) + 8.0 * lb / c->Ns);
-    o.inner_prec_used = S.prec;
-    o.escalations = escalations;
-    o.kernel_launches = c->launches - launches0;
-    if (R[k].status != DWF_OK && result == DWF_OK) result = R[k].status;
-    if (!R[k].converged && result == DWF_OK) result = fail(c, DWF_ENOCONV, "not converged");
+};
+
+// the inner loop of one run until every system is finished
+dwf_status run_loop(SolveRun &r) {
+  while (!r.all_done()) {
+    TRY(r.enqueue_interval());
+    TRY(r.fetch_scalars(r.st));
+    TRY(r.process_interval());
   }
-  return result;
+  return DWF_OK;
+}
+
+// Solve K systems with the same operator; rhs/sol hold K full-lattice arrays one after another.
+dwf_status solve_core(dwf_ctx *c, int K, const double *d_rhs, double *d_sol, dwf_solve_params prm,
+                      dwf_solve_stats *S_out, cudaStream_t st) {
+  SolveRun r(c, K, d_rhs, d_sol, prm, S_out, st);
+  TRY(r.begin());
+  for (;;) {
+    dwf_status loop_st = run_loop(r);
+    if (loop_st != DWF_OK && loop_st != DWF_ENOCONV) return loop_st;
+    bool more = false;
+    TRY(r.after_loop(&more));
+    if (!more) break;
+  }
+  return r.finish();
 }
 
 dwf_status check_solve_args(dwf_ctx *c, dwf_solve_params *prm, const dwf_solve_params *pp, const void *d_rhs,
@@ -1973,6 +2052,172 @@ extern "C" dwf_status dwf_solve_batch(dwf_ctx *c, int nrhs, const double *rhs, d
 extern "C" dwf_status dwf_solve(dwf_ctx *c, const double *rhs, double *sol, const dwf_solve_params *pp,
                                 dwf_solve_stats *stats) {
   return dwf_solve_batch(c, 1, rhs, sol, pp, stats);
+}
+
+// ====================================================================== ragged sets
+
+// A ragged set: one right-hand side on each of n contexts (their own lattice, Ns, masses and
+// weights; typically one gauge field shared by handle), solved together.  Every interval of
+// check_every inner iterations of all unfinished systems is one CUDA graph, a branch per
+// context fork-joined on the caller's stream (the branches run concurrently); restarts,
+// reconstruction and stats stay per context, on the context's own stream, between the
+// graph launches.  Each system takes the same kernels in the same order as it would alone,
+// so its result is the same bit for bit.
+extern "C" dwf_status dwf_solve_ragged_dev(int n, dwf_ctx *const *ctxs, const double *const *d_rhs,
+                                           double *const *d_sol, const dwf_solve_params *pp,
+                                           dwf_solve_stats *stats, void *stream) {
+  if (n < 1 || n > 256 || !ctxs) return DWF_EINVAL;
+  for (int k = 0; k < n; ++k) TRY(check_ctx(ctxs[k]));
+  dwf_ctx *c = ctxs[0];  // errors of the set as a whole are reported on the first context
+  if (!d_rhs || !d_sol) return fail(c, DWF_EINVAL, "null rhs or sol array");
+  std::vector<dwf_solve_params> prm(n);
+  for (int k = 0; k < n; ++k) {
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return fail(c, DWF_EINVAL, "a context appears twice in a ragged set");
+    if (ctxs[k]->device != c->device) return fail(c, DWF_EINVAL, "the contexts of a ragged set must share a device");
+    TRY(check_solve_args(ctxs[k], &prm[k], pp, d_rhs[k], d_sol[k]));
+    if (prm[k].use_x0) return fail(ctxs[k], DWF_EINVAL, "a ragged set takes no initial guess");
+    const size_t full = (size_t)ctxs[k]->V4 * ctxs[k]->Ns * 24 * sizeof(double);
+    const char *a = (const char *)d_rhs[k], *b = (const char *)d_sol[k];
+    if (a < b + full && b < a + full) return fail(ctxs[k], DWF_EINVAL, "rhs and sol overlap");
+  }
+  std::vector<dwf_solve_stats> local;
+  if (!stats) {
+    local.resize(n);
+    stats = local.data();
+  }
+  const cudaStream_t st0 = stream ? (cudaStream_t)stream : c->stream;
+  struct Owned {  // events and the combined graph of this call
+    std::vector<cudaEvent_t> ev;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~Owned() {
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+      for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    }
+    void drop_graph() {
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+      exec = nullptr;
+      graph = nullptr;
+    }
+  } own;
+  own.ev.assign(n + 1, nullptr);
+  for (auto &e : own.ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  // every context's stream starts after the caller's stream (its sources)
+  CK(cudaEventRecord(own.ev[0], st0));
+  for (int k = 0; k < n; ++k) CK(cudaStreamWaitEvent(ctxs[k]->stream, own.ev[0], 0));
+
+  std::vector<std::unique_ptr<SolveRun>> runs;
+  for (int k = 0; k < n; ++k) {
+    runs.emplace_back(new SolveRun(ctxs[k], 1, d_rhs[k], d_sol[k], prm[k], &stats[k], ctxs[k]->stream));
+    TRY(runs[k]->begin());
+  }
+  std::vector<char> pending(n, 1);  // the run has an inner loop (or a tightened pass) to finish
+  std::vector<int> gset;            // the runs the combined graph was captured for
+  for (;;) {
+    std::vector<int> act;
+    for (int k = 0; k < n; ++k)
+      if (pending[k] && !runs[k]->all_done()) act.push_back(k);
+    if (act.empty()) {
+      bool any = false;
+      for (int k = 0; k < n; ++k)
+        if (pending[k]) {
+          bool more = false;
+          TRY(runs[k]->after_loop(&more));
+          pending[k] = more;
+          any = any || more;
+        }
+      if (!any) break;
+      continue;
+    }
+    bool eager = false;  // the first interval of a run (or of its new precision) runs outside a graph
+    for (int k : act) eager = eager || runs[k]->first_batch || !runs[k]->use_graph;
+    if (eager) {
+      for (int k : act) {
+        TRY(runs[k]->record_interval(runs[k]->st));
+        runs[k]->first_batch = false;
+      }
+      for (int k : act) TRY(runs[k]->fetch_scalars(runs[k]->st));
+    } else {
+      bool dirty = !own.exec || act != gset;
+      for (int k : act) dirty = dirty || runs[k]->graph_dirty;
+      if (dirty) {
+        own.drop_graph();
+        CK(cudaStreamBeginCapture(st0, cudaStreamCaptureModeThreadLocal));
+        dwf_status cs = DWF_OK;
+        cudaError_t ce = cudaEventRecord(own.ev[0], st0);
+        for (size_t i = 0; i < act.size() && cs == DWF_OK && ce == cudaSuccess; ++i) {
+          SolveRun &r = *runs[act[i]];
+          ce = cudaStreamWaitEvent(r.st, own.ev[0], 0);
+          const long long l0 = r.c->launches;
+          if (ce == cudaSuccess) cs = r.record_interval(r.st);
+          r.c->launches = l0;
+          if (cs == DWF_OK && ce == cudaSuccess) ce = cudaEventRecord(own.ev[1 + act[i]], r.st);
+          if (cs == DWF_OK && ce == cudaSuccess) ce = cudaStreamWaitEvent(st0, own.ev[1 + act[i]], 0);
+        }
+        const cudaError_t ee = cudaStreamEndCapture(st0, &own.graph);
+        if (cs != DWF_OK) return cs;
+        CK(ce);
+        CK(ee);
+        CK(cudaGraphInstantiate(&own.exec, own.graph, 0));
+        gset = act;
+        for (int k : act) runs[k]->graph_dirty = false;
+      }
+      // the graph starts after each run's last restart and scalar upload on its own stream
+      for (int k : act) {
+        CK(cudaEventRecord(own.ev[1 + k], runs[k]->st));
+        CK(cudaStreamWaitEvent(st0, own.ev[1 + k], 0));
+      }
+      CK(cudaGraphLaunch(own.exec, st0));
+      for (int k : act) runs[k]->c->launches += 5LL * runs[k]->prm.check_every;
+      for (int k : act) TRY(runs[k]->fetch_scalars(st0));
+    }
+    for (int k : act) TRY(runs[k]->process_interval());
+  }
+  dwf_status result = DWF_OK;
+  for (int k = 0; k < n; ++k) {
+    const dwf_status s = runs[k]->finish();
+    if (s != DWF_OK && s != DWF_ENOCONV) return s;
+    if (s != DWF_OK && result == DWF_OK) result = s;
+  }
+  // the caller's stream continues after every solution is written
+  for (int k = 0; k < n; ++k) {
+    CK(cudaEventRecord(own.ev[1 + k], ctxs[k]->stream));
+    CK(cudaStreamWaitEvent(st0, own.ev[1 + k], 0));
+  }
+  return result;
+}
+
+extern "C" dwf_status dwf_solve_ragged(int n, dwf_ctx *const *ctxs, const double *const *rhs, double *const *sol,
+                                       const dwf_solve_params *pp, dwf_solve_stats *stats) {
+  if (n < 1 || n > 256 || !ctxs) return DWF_EINVAL;
+  for (int k = 0; k < n; ++k) TRY(check_ctx(ctxs[k]));
+  dwf_ctx *c = ctxs[0];
+  if (!rhs || !sol) return fail(c, DWF_EINVAL, "null rhs or sol array");
+  std::vector<const double *> din(n);
+  std::vector<double *> dout(n);
+  for (int k = 0; k < n; ++k) {
+    if (!rhs[k] || !sol[k]) return fail(ctxs[k], DWF_EINVAL, "null field pointer");
+    const size_t full = (size_t)ctxs[k]->V4 * ctxs[k]->Ns * 24 * sizeof(double);
+    void *a, *b;
+    TRY(get_raw(ctxs[k], "host_in", full, &a));
+    TRY(get_raw(ctxs[k], "host_out", full, &b));
+    CK(cudaMemcpyAsync(a, rhs[k], full, cudaMemcpyHostToDevice, ctxs[k]->stream));
+    CK(cudaStreamSynchronize(ctxs[k]->stream));
+    din[k] = (const double *)a;
+    dout[k] = (double *)b;
+  }
+  const dwf_status s = dwf_solve_ragged_dev(n, ctxs, din.data(), dout.data(), pp, stats, c->stream);
+  if (s != DWF_OK && s != DWF_ENOCONV) return s;
+  for (int k = 0; k < n; ++k) {
+    const size_t full = (size_t)ctxs[k]->V4 * ctxs[k]->Ns * 24 * sizeof(double);
+    CK(cudaMemcpyAsync(sol[k], dout[k], full, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return s;
 }
 
 // ====================================================================== propagators

@@ -145,6 +145,10 @@ def load(build_if_missing: bool = True):
         "dwf_part_apply": ([i, ctypes.POINTER(vp), i, i, i, dp, dp], i),
         "dwf_part_solve": ([i, ctypes.POINTER(vp), dp, dp, ctypes.POINTER(SolveParams),
                             ctypes.POINTER(SolveStats)], i),
+        "dwf_solve_ragged": ([i, ctypes.POINTER(vp), ctypes.POINTER(dp), ctypes.POINTER(dp),
+                              ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats)], i),
+        "dwf_solve_ragged_dev": ([i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                  ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), vp], i),
         "dwf_cancel": ([vp, ctypes.c_uint64], i),
         "dwf_server_set_admission": ([vp, i], i),
     }
@@ -391,6 +395,47 @@ def dwf_part_solve(parts, rhs, params=None, allow_noconv=False, **kw):
     if not (allow_noconv and rc == DWF_ENOCONV):
         _check(parts[0], rc)
     return sol, st.as_dict()
+
+
+def _check_set(ctxs, st):
+    """Raises for a failed call on a set of contexts, with the first context's message found."""
+    if st != DWF_OK:
+        msg = ""
+        for c in ctxs:
+            msg = load().dwf_last_error(c).decode() if c else ""
+            if msg:
+                break
+        raise DwfError(st, msg)
+
+
+def dwf_solve_ragged(ctxs, rhs, params=None, allow_noconv=False, **kw):
+    """One system per context (a ragged set: each context its own lattice, Ns, masses and
+    weights); rhs[k] is a source of context k.  Returns (list of solutions, list of stats)."""
+    n = len(ctxs)
+    rhs = [_f64(r) for r in rhs]
+    sol = [np.empty_like(r) for r in rhs]
+    p = _params(params, **kw)
+    stats = (SolveStats * n)()
+    DP = ctypes.POINTER(ctypes.c_double)
+    rc = load().dwf_solve_ragged(n, (ctypes.c_void_p * n)(*ctxs), (DP * n)(*[_dp(r) for r in rhs]),
+                                 (DP * n)(*[_dp(x) for x in sol]), ctypes.byref(p), stats)
+    if not (allow_noconv and rc == DWF_ENOCONV):
+        _check_set(ctxs, rc)
+    return sol, [stats[k].as_dict() for k in range(n)]
+
+
+def dwf_solve_ragged_dev(ctxs, d_rhs, d_sol, params=None, stream=None, allow_noconv=False, **kw):
+    """Device-array form of dwf_solve_ragged: d_rhs[k], d_sol[k] device arrays of context k."""
+    n = len(ctxs)
+    p = _params(params, **kw)
+    stats = (SolveStats * n)()
+    VP = ctypes.c_void_p
+    rc = load().dwf_solve_ragged_dev(n, (VP * n)(*ctxs), (VP * n)(*[_ptr(x) for x in d_rhs]),
+                                     (VP * n)(*[_ptr(x) for x in d_sol]), ctypes.byref(p), stats,
+                                     _stream(stream))
+    if not (allow_noconv and rc == DWF_ENOCONV):
+        _check_set(ctxs, rc)
+    return [stats[k].as_dict() for k in range(n)]
 
 
 def dwf_last_error(ctx) -> str:
