@@ -530,11 +530,14 @@ def configs_measure():
     sols = {}
     for kind, inner in (("cosine", "f32"), ("cosine", "bf16"), ("cosine", "f16"), ("borici", "f32")):
         prec = {"f32": dwf.PREC_F32, "bf16": dwf.PREC_BF16, "f16": dwf.PREC_F16}[inner]
-        psi, st = solve(DIMS, NS, kind, MQ, EPS, SEED, eta16, inner_prec=prec)
+        # reliable updates throughout: every inner iteration in the precision named
+        psi, st = solve(DIMS, NS, kind, MQ, EPS, SEED, eta16, inner_prec=prec, mode=dwf.MODE_RELIABLE)
         if kind == "cosine":
             sols[inner] = psi
-        rows.append({"config": f"16^3x32x16 {kind} mq 0.02", "inner": inner, "iters": st["iters"],
-                     "restarts": st["restarts"], "solve_ms": st["time_ms"], "true_res_library": st["true_res_full"]})
+        rows.append({"config": f"16^3x32x16 {kind} mq 0.02", "inner": inner, "mode": "reliable",
+                     "delta": 0.3 if inner == "f16" else 0.01, "iters": st["iters"],
+                     "restarts": st["restarts"], "escalations": st["escalations"], "solve_ms": st["time_ms"],
+                     "true_res_library": st["true_res_full"]})
         jobs.append((len(rows) - 1, (DIMS, NS, EPS, SEED, MQ, kind, eta16, psi)))
     for inner in ("bf16", "f16"):
         rows[[r["inner"] for r in rows].index(inner)]["rel_diff_vs_f32"] = float(

@@ -99,7 +99,8 @@ enum {
 typedef struct {
     double tol;        /* stop when |b - C C^dag x| <= tol |b| in FP64 (default 1e-10) */
     double delta;      /* reliable-update trigger: restart when |r| < delta * max|r| since the
-                          last restart; <= 0 selects the default, 0.01 */
+                          last restart; <= 0 selects the default of the inner precision:
+                          0.3 for fp16, 0.01 otherwise */
     int max_iter;      /* cap on inner CG iterations (default 100000) */
     int inner_prec;    /* DWF_PREC_* of the inner CG (default DWF_PREC_F32) */
     int mode;          /* DWF_MODE_* (default DWF_MODE_AUTO) */
@@ -313,7 +314,7 @@ dwf_status dwf_part_apply(int nparts, dwf_ctx *const *parts, int op, int prec, i
  * rhs = eta, or C C^dag x = b on params->schur_parity) for a global full-lattice host rhs,
  * the solution written to the global host array sol.  Inner CG (Algorithm 1) in
  * params->inner_prec with FP64 reliable updates (Sec. 2.3: restart when |r| falls by
- * params->delta, default 0.01, or reaches the target), every reduction summed over the
+ * params->delta, default 0.3 for fp16 and 0.01 otherwise, or reaches the target), every reduction summed over the
  * parts in FP64 (the allreduce of a multi-GPU run: 2 per iteration), faces exchanged before
  * every hop.  The host steers each iteration (no CUDA graphs) and a full solve takes no
  * tightened second pass: DWF_ENOCONV if |eta - D psi| / |eta| misses tol.  stats (if not

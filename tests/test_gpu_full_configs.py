@@ -55,11 +55,14 @@ def test_config2_precision_sweep_full_size(lattice16, prec):
     dims, ns, U, eta = lattice16
     mq = 0.02
     om, sg = inputs.weights("cosine", ns)
+    # reliable updates throughout (no switch to defect correction, no escalation to FP32):
+    # every inner iteration in the precision under test
     with dwf.Context(dims, ns, M0, mq, om, sg, U) as ctx:
-        psi, st = dwf.dwf_solve(ctx.h, eta, inner_prec=prec, tol=1e-10)
+        psi, st = dwf.dwf_solve(ctx.h, eta, inner_prec=prec, tol=1e-10, mode=dwf.MODE_RELIABLE)
     res = oracle_residual(dims, ns, U, mq, om, sg, eta, psi)
     assert res <= 1e-10, f"oracle true residual {res:.3e}, stats {st}"
     assert st["converged"] == 1
+    assert st["escalations"] == 0 and st["inner_prec_used"] == prec and st["mode_used"] == dwf.MODE_RELIABLE
     _SWEEP[prec] = psi
     if prec != 1 and 1 in _SWEEP:
         ref = _SWEEP[1]
