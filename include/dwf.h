@@ -58,7 +58,8 @@ typedef enum {
     DWF_EAGAIN = 5,   /* poll: request not finished yet */
     DWF_ETIMEOUT = 6, /* a bounded device-side wait gave up (kernel error word set) */
     DWF_ECUDA = 7,    /* a CUDA runtime call failed; see dwf_last_error */
-    DWF_ENOGAUGE = 8  /* operator used before dwf_load_gauge */
+    DWF_ENOGAUGE = 8, /* operator used before dwf_load_gauge */
+    DWF_ECOMM = 9     /* a dwf_part_comm callback reported failure */
 } dwf_status;
 
 /* operators of dwf_apply_eo */
@@ -321,6 +322,34 @@ dwf_status dwf_part_apply(int nparts, dwf_ctx *const *parts, int op, int prec, i
  * NULL): iterations, restarts, true residuals (FP64), counted flops, host wall time. */
 dwf_status dwf_part_solve(int nparts, dwf_ctx *const *parts, const double *rhs, double *sol,
                           const dwf_solve_params *params, dwf_solve_stats *stats);
+
+/* The transport between parts held by different processes (one part each, e.g. one per
+ * GPU): the library packs its part's cut faces and takes its block's sums, the caller moves
+ * them.  Every part calls each callback the same number of times in the same order (they
+ * are collective), from the thread of the library call.
+ *   exchange: for each k = 2 mu + side with bytes[k] > 0 (direction mu cut; side 0: the face
+ *     x_mu = 0, 1: the face x_mu = L_mu - 1 of the local block), send the bytes[k] bytes at
+ *     send[k] to the part on that side (grid coordinate coord[mu] - 1 or + 1, periodic), and
+ *     receive into recv[k] the bytes[k] bytes that this part's neighbour on that side sends
+ *     towards it (its face k ^ 1).  send and recv are pinned host memory owned by the library
+ *     and valid for the call; a grid of 2 along mu makes both neighbours the same part.
+ *   allreduce: replace v[0..n) by its sum over all parts, identical on every part.
+ * Each returns 0 on success; any other value fails the library call with DWF_ECOMM. */
+typedef struct {
+    void *user;
+    int (*exchange)(void *user, const void *const *send, void *const *recv, const size_t *bytes);
+    int (*allreduce)(void *user, double *v, int n);
+} dwf_part_comm;
+/* dwf_part_apply for this part alone, the others reached through comm: in and out are this
+ * part's block in the host layout of its local extents (global_dims / grid, x fastest). */
+dwf_status dwf_part_apply_comm(dwf_ctx *part, const dwf_part_comm *comm, int op, int prec, int parity,
+                               const double *in, double *out);
+/* dwf_part_solve for this part alone, the others reached through comm: rhs and sol are this
+ * part's block in the host layout of its local extents.  Every decision (restart, convergence)
+ * is taken on allreduced sums, so iterations, residuals and the status are the same on every
+ * part; with two parts the result equals dwf_part_solve's bit for bit. */
+dwf_status dwf_part_solve_comm(dwf_ctx *part, const dwf_part_comm *comm, const double *rhs, double *sol,
+                               const dwf_solve_params *params, dwf_solve_stats *stats);
 
 /* The launch shape the autotuner chose for inner-CG kernel class `kclass` (DWF_KC_HOP_M5,
  * DWF_KC_HOP_XPAY or DWF_KC_HOP_UPDATE) at precision `prec` (FP32, F16, BF16) for this

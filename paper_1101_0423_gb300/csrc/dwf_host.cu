@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -110,6 +111,7 @@ const char *status_name(dwf_status s) {
     case DWF_ETIMEOUT: return "DWF_ETIMEOUT";
     case DWF_ECUDA: return "DWF_ECUDA";
     case DWF_ENOGAUGE: return "DWF_ENOGAUGE";
+    case DWF_ECOMM: return "DWF_ECOMM";
   }
   return "DWF_UNKNOWN";
 }
@@ -886,6 +888,7 @@ dwf_status dwf_destroy(dwf_ctx *c) {
   }
   pinned_put(c->h_sc, sizeof(CGScalars));
   pinned_put(c->h_scb, c->h_scb_cap * sizeof(CGScalars));
+  pinned_put(c->h_face, c->h_face_bytes);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -2512,9 +2515,13 @@ cudaError_t part_unpack_any(int prec, dwf_ctx *c, const void *buf, Field out, lo
 }
 
 // the parts of one decomposed lattice, indexed by their grid coordinates
+// the parts of one decomposed lattice that this call drives: every part, in grid order
+// (at[x + gx (y + gy (z + gz t))]), or -- with a caller's transport, comm -- this process's
+// one part, the others reached through comm
 struct PartSet {
-  std::vector<dwf_ctx *> at;  // at[x + gx (y + gy (z + gz t))]
+  std::vector<dwf_ctx *> at;
   int grid[4];
+  const dwf_part_comm *comm = nullptr;
   dwf_ctx *get(const int (&c)[4]) const {
     int k[4];
     for (int mu = 0; mu < 4; ++mu) k[mu] = (c[mu] % grid[mu] + grid[mu]) % grid[mu];
@@ -2522,8 +2529,57 @@ struct PartSet {
   }
 };
 
+// part_exchange through the caller's transport: this process's part packs its cut faces
+// into pinned host memory (face k = 2 mu + side), comm->exchange swaps them with the
+// neighbours, and the received faces are unpacked into the halo slots
+dwf_status part_exchange_comm(const PartSet &ps, const std::string &name, int prec, int q) {
+  dwf_ctx *c = ps.at[0];
+  Field f;
+  TRY(part_field(c, name, prec, &f));
+  size_t bytes[8] = {}, off[8] = {}, total = 0;
+  for (int k = 0; k < 8; ++k) {
+    if (c->pg.grid[k >> 1] == 1) continue;
+    bytes[k] = (size_t)c->pg.fsz[k >> 1] * c->Ns * 12 * real_bytes(prec);
+    off[k] = total;
+    total += (bytes[k] + 15) & ~(size_t)15;
+  }
+  if (total == 0) return DWF_OK;  // no cut direction: a single part
+  if (c->h_face_bytes < 2 * total) {
+    pinned_put(c->h_face, c->h_face_bytes);
+    c->h_face = pinned_get(2 * total);
+    c->h_face_bytes = c->h_face ? 2 * total : 0;
+    if (!c->h_face) return fail(c, DWF_ENOMEM, "pinned host memory for the faces");
+  }
+  char *hs = static_cast<char *>(c->h_face), *hr = hs + total;
+  const void *send[8] = {};
+  void *recv[8] = {};
+  for (int k = 0; k < 8; ++k) {
+    if (!bytes[k]) continue;
+    void *d;
+    TRY(get_raw(c, "part_send" + std::to_string(k), bytes[k], &d));
+    CK(part_pack_any(prec, c, f, k >> 1, k & 1, q, d, c->stream));
+    CK(cudaMemcpyAsync(hs + off[k], d, bytes[k], cudaMemcpyDeviceToHost, c->stream));
+    send[k] = hs + off[k];
+    recv[k] = hr + off[k];
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if (ps.comm->exchange(ps.comm->user, send, recv, bytes) != 0)
+    return fail(c, DWF_ECOMM, "the exchange callback failed");
+  for (int k = 0; k < 8; ++k) {
+    if (!bytes[k]) continue;
+    // the halo slab on side k & 1 takes that neighbour's face k ^ 1
+    void *d;
+    TRY(get_raw(c, "part_recv" + std::to_string(k), bytes[k], &d));
+    CK(cudaMemcpyAsync(d, hr + off[k], bytes[k], cudaMemcpyHostToDevice, c->stream));
+    CK(part_unpack_any(prec, c, d, f, c->h + c->pg.foff[k >> 1][k & 1], c->pg.fsz[k >> 1], c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return DWF_OK;
+}
+
 // every part's field `name` (parity q) gets its halo slots from the neighbouring parts
 dwf_status part_exchange(const PartSet &ps, const std::string &name, int prec, int q) {
+  if (ps.comm) return part_exchange_comm(ps, name, prec, q);
   // 1. pack the cut faces
   for (dwf_ctx *c : ps.at) {
     Field f;
@@ -2631,6 +2687,51 @@ dwf_status part_set(int nparts, dwf_ctx *const *parts, int prec, PartSet *ps) {
   return DWF_OK;
 }
 
+// this process's part under the caller's transport: the same checks as part_set for one part
+dwf_status part_set_comm(dwf_ctx *c, const dwf_part_comm *comm, int prec, PartSet *ps) {
+  if (!c->part) return fail(c, DWF_EINVAL, "not a partitioned context");
+  if (!comm || !comm->exchange || !comm->allreduce) return fail(c, DWF_EINVAL, "null transport or callback");
+  for (int mu = 0; mu < 4; ++mu) ps->grid[mu] = c->pg.grid[mu];
+  ps->at.assign(1, c);
+  ps->comm = comm;
+  TRY(ensure_part_gauge(c, prec));
+  TRY(ensure_part_gauge(c, P_F64));
+  return DWF_OK;
+}
+
+// one part's field `name` (parity p) from its block in the local host layout, or into it
+dwf_status part_scatter_local(dwf_ctx *c, const double *in, const std::string &name, int prec, int p) {
+  const size_t n = (size_t)2 * c->pg.h * c->Ns * 24;
+  void *d;
+  TRY(get_raw(c, "part_host", n * sizeof(double), &d));
+  CK(cudaMemcpyAsync(d, in, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  Field f;
+  TRY(part_field(c, name, prec, &f));
+  CK(pack_any(prec, static_cast<const double *>(d), f, local_geom(c->pg, c->Ns), p, c->sm_count, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return DWF_OK;
+}
+dwf_status part_gather_local(dwf_ctx *c, const std::string &name, int prec, int p, double *out) {
+  const size_t n = (size_t)2 * c->pg.h * c->Ns * 24;
+  void *d;
+  TRY(get_raw(c, "part_host", n * sizeof(double), &d));
+  CK(cudaMemcpyAsync(d, out, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  Field f;
+  TRY(part_field(c, name, prec, &f));
+  CK(unpack_any(prec, f, static_cast<double *>(d), local_geom(c->pg, c->Ns), p, c->sm_count, c->stream));
+  CK(cudaMemcpyAsync(out, d, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return DWF_OK;
+}
+
+// where the caller's source comes from and the result goes: the global host arrays of
+// dwf_part_apply / dwf_part_solve, or one part's local block under a transport
+struct PartIO {
+  std::function<dwf_status(const std::string &, int, int)> scatter;  // (field, prec, parity)
+  std::function<dwf_status(const std::string &, int, int)> gather;   // into the output's sites of the parity
+  std::function<void()> zero;                                       // the output set to 0
+};
+
 // every part's share of a global full-lattice host array into its field `name` (parity p)
 dwf_status part_scatter(const PartSet &ps, const double *g_in, const std::string &name, int prec, int p) {
   std::vector<double> buf;
@@ -2731,20 +2832,20 @@ extern "C" dwf_status dwf_load_gauge_part(dwf_ctx *c, const double *U) {
   return DWF_OK;
 }
 
-extern "C" dwf_status dwf_part_apply(int nparts, dwf_ctx *const *parts, int op, int prec, int parity,
-                                     const double *in, double *out) {
-  if (nparts < 1 || !parts || !parts[0] || !in || !out) return DWF_EINVAL;
-  dwf_ctx *c0 = parts[0];
-  TRY(check_ctx(c0));
+namespace {
+
+dwf_status check_part_op(dwf_ctx *c0, int op, int prec, int parity) {
   if (!valid_prec(prec)) return fail(c0, DWF_EINVAL, "unknown precision");
   if (op < DWF_OP_DEO || op > DWF_OP_CCDAG || op == DWF_OP_M5 || op == DWF_OP_M5T)
     return fail(c0, DWF_EINVAL, "dwf_part_apply applies DEO, DOE, C, CDAG or CCDAG");
   if (op >= DWF_OP_C && parity != 0 && parity != 1) return fail(c0, DWF_EINVAL, "parity must be 0 or 1");
-  PartSet ps;
-  TRY(part_set(nparts, parts, prec, &ps));
+  return DWF_OK;
+}
+
+dwf_status part_apply_core(const PartSet &ps, const PartIO &io, int op, int prec, int parity) {
   const int inpar = op == DWF_OP_DEO ? 1 : op == DWF_OP_DOE ? 0 : parity;
   const int outpar = op == DWF_OP_DEO ? 0 : op == DWF_OP_DOE ? 1 : parity;
-  TRY(part_scatter(ps, in, "in", prec, inpar));
+  TRY(io.scatter("in", prec, inpar));
   const int sp = parity, opp = 1 - parity;
   switch (op) {
     case DWF_OP_DEO:
@@ -2774,9 +2875,53 @@ extern "C" dwf_status dwf_part_apply(int nparts, dwf_ctx *const *parts, int op, 
       break;
     }
   }
-  const int *G = c0->pg.G;
-  memset(out, 0, (size_t)G[0] * G[1] * G[2] * G[3] * c0->Ns * 24 * sizeof(double));
-  return part_gather(ps, "out", prec, outpar, out);
+  io.zero();
+  return io.gather("out", prec, outpar);
+}
+
+// the global host arrays of dwf_part_apply / dwf_part_solve
+PartIO global_io(const PartSet &ps, const double *in, double *out) {
+  dwf_ctx *c0 = ps.at[0];
+  PartIO io;
+  io.scatter = [&ps, in](const std::string &name, int prec, int p) { return part_scatter(ps, in, name, prec, p); };
+  io.gather = [&ps, out](const std::string &name, int prec, int p) { return part_gather(ps, name, prec, p, out); };
+  io.zero = [c0, out]() {
+    const int *G = c0->pg.G;
+    memset(out, 0, (size_t)G[0] * G[1] * G[2] * G[3] * c0->Ns * 24 * sizeof(double));
+  };
+  return io;
+}
+
+// one part's local blocks under a transport
+PartIO local_io(dwf_ctx *c, const double *in, double *out) {
+  PartIO io;
+  io.scatter = [c, in](const std::string &name, int prec, int p) { return part_scatter_local(c, in, name, prec, p); };
+  io.gather = [c, out](const std::string &name, int prec, int p) { return part_gather_local(c, name, prec, p, out); };
+  io.zero = [c, out]() { memset(out, 0, (size_t)2 * c->pg.h * c->Ns * 24 * sizeof(double)); };
+  return io;
+}
+
+}  // namespace
+
+extern "C" dwf_status dwf_part_apply(int nparts, dwf_ctx *const *parts, int op, int prec, int parity,
+                                     const double *in, double *out) {
+  if (nparts < 1 || !parts || !parts[0] || !in || !out) return DWF_EINVAL;
+  dwf_ctx *c0 = parts[0];
+  TRY(check_ctx(c0));
+  TRY(check_part_op(c0, op, prec, parity));
+  PartSet ps;
+  TRY(part_set(nparts, parts, prec, &ps));
+  return part_apply_core(ps, global_io(ps, in, out), op, prec, parity);
+}
+
+extern "C" dwf_status dwf_part_apply_comm(dwf_ctx *part, const dwf_part_comm *comm, int op, int prec, int parity,
+                                          const double *in, double *out) {
+  TRY(check_ctx(part));
+  if (!in || !out) return fail(part, DWF_EINVAL, "null field pointer");
+  TRY(check_part_op(part, op, prec, parity));
+  PartSet ps;
+  TRY(part_set_comm(part, comm, prec, &ps));
+  return part_apply_core(ps, local_io(part, in, out), op, prec, parity);
 }
 
 namespace {
@@ -2789,6 +2934,8 @@ dwf_status part_sum(const PartSet &ps, int slot, double *out) {
     TRY(pull_scalars(c, c->stream));
     s += slot ? c->h_sc->red2 : c->h_sc->red;
   }
+  if (ps.comm && ps.comm->allreduce(ps.comm->user, &s, 1) != 0)
+    return fail(ps.at[0], DWF_ECOMM, "the allreduce callback failed");
   *out = s;
   return DWF_OK;
 }
@@ -2843,26 +2990,29 @@ dwf_status part_resid64(const PartSet &ps, int sp, double *rr) {
 
 }  // namespace
 
-extern "C" dwf_status dwf_part_solve(int nparts, dwf_ctx *const *parts, const double *rhs, double *sol,
-                                     const dwf_solve_params *pp, dwf_solve_stats *stats) {
-  if (nparts < 1 || !parts || !parts[0] || !rhs || !sol) return DWF_EINVAL;
-  dwf_ctx *c0 = parts[0];
-  TRY(check_ctx(c0));
-  dwf_solve_params prm;
-  if (pp) prm = *pp;
-  else dwf_solve_params_default(&prm);
-  if (!(prm.tol > 0.0) || !valid_prec(prm.inner_prec) || (prm.system != DWF_SYS_FULL && prm.system != DWF_SYS_NORMAL) ||
-      (prm.schur_parity != 0 && prm.schur_parity != 1) || prm.max_iter < 1)
+namespace {
+
+dwf_status part_solve_params(dwf_ctx *c0, const dwf_solve_params *pp, dwf_solve_params *prm) {
+  if (pp) *prm = *pp;
+  else dwf_solve_params_default(prm);
+  if (!(prm->tol > 0.0) || !valid_prec(prm->inner_prec) ||
+      (prm->system != DWF_SYS_FULL && prm->system != DWF_SYS_NORMAL) ||
+      (prm->schur_parity != 0 && prm->schur_parity != 1) || prm->max_iter < 1)
     return fail(c0, DWF_EINVAL, "invalid solve parameters");
+  return DWF_OK;
+}
+
+// the solve across the parts of ps (all of them, or this process's one under a transport)
+dwf_status part_solve_core(const PartSet &ps, const PartIO &io, const dwf_solve_params &prm,
+                           dwf_solve_stats *stats) {
+  dwf_ctx *c0 = ps.at[0];
   const int P = prm.inner_prec, sp = prm.schur_parity, opp = 1 - sp;
   const bool full = prm.system == DWF_SYS_FULL;
   const double delta = prm.delta > 0.0 ? prm.delta : default_delta(prm.inner_prec);
-  PartSet ps;
-  TRY(part_set(nparts, parts, P, &ps));
   const auto t0 = std::chrono::steady_clock::now();
   // ---- the Schur-parity source (Eq. 10 for the full system): b = eta'_sp - M5 D eta'_op
   if (full) {
-    for (int p = 0; p < 2; ++p) TRY(part_scatter(ps, rhs, "eta" + std::to_string(p), P_F64, p));
+    for (int p = 0; p < 2; ++p) TRY(io.scatter("eta" + std::to_string(p), P_F64, p));
     for (dwf_ctx *c : ps.at)
       for (int p = 0; p < 2; ++p) {
         Field e, ep;
@@ -2872,7 +3022,7 @@ extern "C" dwf_status dwf_part_solve(int nparts, dwf_ctx *const *parts, const do
       }
     TRY(part_hop(ps, P_F64, E_M_XPAY, "etap" + std::to_string(opp), "b", "etap" + std::to_string(sp), sp, 1, 0.5));
   } else {
-    TRY(part_scatter(ps, rhs, "b", P_F64, sp));
+    TRY(io.scatter("b", P_F64, sp));
   }
   double bnorm2 = 0;
   TRY(part_norm2(ps, "b", P_F64, &bnorm2));
@@ -3004,10 +3154,9 @@ extern "C" dwf_status dwf_part_solve(int nparts, dwf_ctx *const *parts, const do
         TRY(part_field(c, "z" + std::to_string(p), P_F64, &z));
         TRY(smix(c, c->stream, P_F64, S_DUAL, psi, t, MK_W, 1.0, DWF_KC_F64, z, MK_Z));
       }
-    const int *G = c0->pg.G;
-    memset(sol, 0, (size_t)G[0] * G[1] * G[2] * G[3] * c0->Ns * 24 * sizeof(double));
+    io.zero();
     for (int p = 0; p < 2; ++p) {
-      TRY(part_gather(ps, "psi" + std::to_string(p), P_F64, p, sol));
+      TRY(io.gather("psi" + std::to_string(p), P_F64, p));
       TRY(part_hop(ps, P_F64, E_XPAY, "tt" + std::to_string(1 - p), "dpsi" + std::to_string(p),
                    "z" + std::to_string(p), p, 0, -0.5));
     }
@@ -3034,9 +3183,8 @@ extern "C" dwf_status dwf_part_solve(int nparts, dwf_ctx *const *parts, const do
     }
     res_full = den > 0 ? sqrt(num / den) : 0.0;
   } else {
-    const int *G = c0->pg.G;
-    memset(sol, 0, (size_t)G[0] * G[1] * G[2] * G[3] * c0->Ns * 24 * sizeof(double));
-    TRY(part_gather(ps, "xh", P_F64, sp, sol));
+    io.zero();
+    TRY(io.gather("xh", P_F64, sp));
   }
   if (stats) {
     memset(stats, 0, sizeof(*stats));
@@ -3055,4 +3203,29 @@ extern "C" dwf_status dwf_part_solve(int nparts, dwf_ctx *const *parts, const do
   if (!converged) return fail(c0, DWF_ENOCONV, "max_iter reached");
   if (full && res_full > prm.tol) return fail(c0, DWF_ENOCONV, "full-system residual above tol");
   return DWF_OK;
+}
+
+}  // namespace
+
+extern "C" dwf_status dwf_part_solve(int nparts, dwf_ctx *const *parts, const double *rhs, double *sol,
+                                     const dwf_solve_params *pp, dwf_solve_stats *stats) {
+  if (nparts < 1 || !parts || !parts[0] || !rhs || !sol) return DWF_EINVAL;
+  dwf_ctx *c0 = parts[0];
+  TRY(check_ctx(c0));
+  dwf_solve_params prm;
+  TRY(part_solve_params(c0, pp, &prm));
+  PartSet ps;
+  TRY(part_set(nparts, parts, prm.inner_prec, &ps));
+  return part_solve_core(ps, global_io(ps, rhs, sol), prm, stats);
+}
+
+extern "C" dwf_status dwf_part_solve_comm(dwf_ctx *part, const dwf_part_comm *comm, const double *rhs, double *sol,
+                                          const dwf_solve_params *pp, dwf_solve_stats *stats) {
+  TRY(check_ctx(part));
+  if (!rhs || !sol) return fail(part, DWF_EINVAL, "null field pointer");
+  dwf_solve_params prm;
+  TRY(part_solve_params(part, pp, &prm));
+  PartSet ps;
+  TRY(part_set_comm(part, comm, prm.inner_prec, &ps));
+  return part_solve_core(ps, local_io(part, rhs, sol), prm, stats);
 }

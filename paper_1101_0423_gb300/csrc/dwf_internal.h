@@ -105,6 +105,10 @@ struct dwf_ctx {
   bool part = false;
   dwf::PartGeom pg{};
   double *d_Ug = nullptr;
+  // pinned host staging of the packed faces for a caller's transport (dwf_part_*_comm):
+  // the eight send faces, then the eight receive faces
+  void *h_face = nullptr;
+  size_t h_face_bytes = 0;
   // profiling of the current call
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;

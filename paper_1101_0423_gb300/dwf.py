@@ -24,9 +24,9 @@ SYS_FULL, SYS_NORMAL = range(2)
 KC_NAMES = ["hop_m5", "hop_xpay", "hop_update", "smix_p", "f64", "other"]
 KC_HOP_M5, KC_HOP_XPAY, KC_HOP_UPDATE = range(3)
 STATUS = ["DWF_OK", "DWF_EINVAL", "DWF_ENOMEM", "DWF_ENOCONV", "DWF_EBUSY", "DWF_EAGAIN",
-          "DWF_ETIMEOUT", "DWF_ECUDA", "DWF_ENOGAUGE"]
+          "DWF_ETIMEOUT", "DWF_ECUDA", "DWF_ENOGAUGE", "DWF_ECOMM"]
 DWF_OK, DWF_EINVAL, DWF_ENOMEM, DWF_ENOCONV, DWF_EBUSY, DWF_EAGAIN, DWF_ETIMEOUT, DWF_ECUDA, \
-    DWF_ENOGAUGE = range(9)
+    DWF_ENOGAUGE, DWF_ECOMM = range(10)
 
 
 class DwfError(RuntimeError):
@@ -62,6 +62,16 @@ class SolveStats(ctypes.Structure):
 
 class Partition(ctypes.Structure):
     _fields_ = [("global_dims", ctypes.c_int * 4), ("grid", ctypes.c_int * 4), ("coord", ctypes.c_int * 4)]
+
+
+# callbacks of dwf_part_comm (the transport between parts held by different processes)
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                               ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_size_t))
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int)
+
+
+class PartComm(ctypes.Structure):
+    _fields_ = [("user", ctypes.c_void_p), ("exchange", EXCHANGE_FN), ("allreduce", ALLREDUCE_FN)]
 
 
 class ServerParams(ctypes.Structure):
@@ -149,6 +159,9 @@ def load(build_if_missing: bool = True):
                               ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats)], i),
         "dwf_solve_ragged_dev": ([i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                   ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), vp], i),
+        "dwf_part_apply_comm": ([vp, ctypes.POINTER(PartComm), i, i, i, dp, dp], i),
+        "dwf_part_solve_comm": ([vp, ctypes.POINTER(PartComm), dp, dp, ctypes.POINTER(SolveParams),
+                                 ctypes.POINTER(SolveStats)], i),
         "dwf_cancel": ([vp, ctypes.c_uint64], i),
         "dwf_server_set_admission": ([vp, i], i),
     }
@@ -436,6 +449,58 @@ def dwf_solve_ragged_dev(ctxs, d_rhs, d_sol, params=None, stream=None, allow_noc
     if not (allow_noconv and rc == DWF_ENOCONV):
         _check_set(ctxs, rc)
     return [stats[k].as_dict() for k in range(n)]
+
+
+def part_comm(exchange, allreduce) -> PartComm:
+    """A dwf_part_comm from two Python callables: exchange(send, recv) with send[k] / recv[k]
+    (k = 2 mu + side) uint8 numpy views of the library's face buffers, None where nothing
+    moves; allreduce(v) summing the float64 array v over all parts in place.  An exception
+    in either fails the library call with DWF_ECOMM.  Keep the returned object alive while
+    the library may call it."""
+    def _exchange(user, send, recv, nbytes):
+        try:
+            s, r = [None] * 8, [None] * 8
+            for k in range(8):
+                n = int(nbytes[k])
+                if n:
+                    s[k] = np.ctypeslib.as_array((ctypes.c_uint8 * n).from_address(send[k]))
+                    r[k] = np.ctypeslib.as_array((ctypes.c_uint8 * n).from_address(recv[k]))
+            exchange(s, r)
+            return 0
+        except Exception:
+            return 1
+
+    def _allreduce(user, v, n):
+        try:
+            allreduce(np.ctypeslib.as_array(v, shape=(int(n),)))
+            return 0
+        except Exception:
+            return 1
+
+    c = PartComm(None, EXCHANGE_FN(_exchange), ALLREDUCE_FN(_allreduce))
+    c._keep = (_exchange, _allreduce)
+    return c
+
+
+def dwf_part_apply_comm(part, comm, op, prec, parity, x) -> np.ndarray:
+    """dwf_part_apply for this process's part alone; x and the result are its local block."""
+    x = _f64(x)
+    out = np.empty_like(x)
+    _check(part, load().dwf_part_apply_comm(part, ctypes.byref(comm), int(op), int(prec), int(parity), _dp(x),
+                                            _dp(out)))
+    return out
+
+
+def dwf_part_solve_comm(part, comm, rhs, params=None, allow_noconv=False, **kw):
+    """dwf_part_solve for this process's part alone; (local solution block, stats dict)."""
+    rhs = _f64(rhs)
+    sol = np.empty_like(rhs)
+    p = _params(params, **kw)
+    st = SolveStats()
+    rc = load().dwf_part_solve_comm(part, ctypes.byref(comm), _dp(rhs), _dp(sol), ctypes.byref(p), ctypes.byref(st))
+    if not (allow_noconv and rc == DWF_ENOCONV):
+        _check(part, rc)
+    return sol, st.as_dict()
 
 
 def dwf_last_error(ctx) -> str:
