@@ -262,7 +262,7 @@ def serve_run(reqs, lam, gauges_np, inner_prec, max_inflight=4, budget_gb=150.0,
         handles = {d: dwf.dwf_server_add_gauge(srv, d, U) for d, U in gauges_np.items()}
         gaps = -np.log(1.0 - inputs.uniforms(seed, inputs.TAG_ARRIVALS, len(reqs))) / lam
         rhs = [inputs.gaussian_source(r["dims"], r["Ns"], seed=r["rhs_seed"]) for r in reqs]
-        pending, statuses = [], []
+        pending, statuses, escalated = [], [], 0
         t0 = time.perf_counter()
         next_t = t0
         for r, g, b in zip(reqs, gaps, rhs):
@@ -280,10 +280,13 @@ def serve_run(reqs, lam, gauges_np, inner_prec, max_inflight=4, budget_gb=150.0,
                     left.append(t)
                 else:
                     statuses.append(res[1]["status"])
+                    escalated += res[1]["stats"]["escalations"] > 0
             pending = left
             time.sleep(0.002)
         st = dwf.dwf_server_get_stats(srv)
         st["ok"] = sum(1 for x in statuses if x == dwf.DWF_OK)
+        # 16-bit solves in AUTO mode that switched to FP32 inner iterations partway
+        st["escalated_to_f32"] = escalated
         return st
     finally:
         dwf.dwf_server_destroy(srv)
@@ -309,7 +312,7 @@ def serve_measure(n, lattices, inner_prec, fractions, progress=False):
         yield {"lambda_fraction": f, "lambda_per_s": f * capacity, "capacity_per_s": capacity,
                "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                "mean_ms": st["mean_ms"], "completed": st["completed"], "ok": st["ok"],
-               "batched": st["batched"]}
+               "batched": st["batched"], "escalated_to_f32": st["escalated_to_f32"]}
 
 
 def odwf_measure(repeats=3):
@@ -782,8 +785,10 @@ def main():
         out["served"] = {"solves_per_s": row["solves_per_s"], "p50_ms": row["p50_ms"], "p99_ms": row["p99_ms"],
                          "lambda_per_s": row["lambda_per_s"], "capacity_per_s": row["capacity_per_s"],
                          "requests": row["completed"], "ok": row["ok"],
+                         "escalated_to_f32": row["escalated_to_f32"],
                          "sample": "12 requests, uniform lattice {8^4,12^3x24,16^3x32} x Ns {8,16,24,32} x "
-                                   "mq U[0.005,0.1] x {shamir,borici,cosine}, bf16 inner, tol 1e-10, "
+                                   "mq U[0.005,0.1] x {shamir,borici,cosine}, bf16 inner (AUTO mode: a "
+                                   "solve whose bf16 cycles fail continues in FP32), tol 1e-10, "
                                    "Poisson arrivals at 0.8 x single-stream capacity, 4 slots, 150 GB budget"}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_sample(s0["iters"], s0["restarts"])
