@@ -272,8 +272,7 @@ dwf_status dwf_propagator_dev(dwf_ctx *ctx, const int x0[4], const dwf_solve_par
  *   - the gauge field of `prec` must already exist (dwf_load_gauge builds FP64 and FP32; one
  *     dwf_apply_eo_dev call builds a 16-bit form), else DWF_EINVAL;
  *   - set-up: the first call on a context looks up the array's device address
- *     (cudaGetSymbolAddress) with the context's device current; that first call should
- *     come before any stream capture;
+ *     (cudaGetSymbolAddress) with the context's device current;
  *   - the call returns when its work is done: it synchronises `stream` and copies the
  *     kernels' 4-byte error word to the host (DWF_ETIMEOUT if a bounded device-side wait
  *     gave up);
