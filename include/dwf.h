@@ -333,7 +333,10 @@ dwf_status dwf_part_solve(int nparts, dwf_ctx *const *parts, const double *rhs, 
  *     towards it (its face k ^ 1).  send and recv are pinned host memory owned by the library
  *     and valid for the call; a grid of 2 along mu makes both neighbours the same part.
  *   allreduce: replace v[0..n) by its sum over all parts, identical on every part.
- * Each returns 0 on success; any other value fails the library call with DWF_ECOMM. */
+ * Each returns 0 on success; any other value fails the library call with DWF_ECOMM.  A part
+ * whose call fails before a collective step (an invalid argument, a missing gauge field)
+ * leaves the others waiting in that step: the transport's own timeout has to end their wait
+ * (and return non-zero). */
 typedef struct {
     void *user;
     int (*exchange)(void *user, const void *const *send, void *const *recv, const size_t *bytes);

@@ -4,6 +4,8 @@ A part's rank is its grid position in lexicographic order, x fastest.  The libra
 spin-projected faces and takes the block sums; this module only moves them: each face with
 a point-to-point message tagged by its face index k = 2 mu + side, each sum with all_reduce
 (the same result on every rank)."""
+import datetime
+
 import torch
 import torch.distributed as dist
 
@@ -25,10 +27,14 @@ def grid_coord(rank, grid) -> list:
 
 
 class TorchPartComm:
-    """The dwf_part_comm of the part at `coord` of `grid` (pass .comm to dwf_part_*_comm)."""
+    """The dwf_part_comm of the part at `coord` of `grid` (pass .comm to dwf_part_*_comm).
+    timeout (seconds): how long a face message may take before the exchange fails (the
+    library call then returns DWF_ECOMM), so that a part whose peer has failed does not wait
+    for ever; None leaves it to the process group."""
 
-    def __init__(self, grid, coord, group=None):
+    def __init__(self, grid, coord, group=None, timeout=None):
         self.grid, self.coord, self.group = list(grid), list(coord), group
+        self.timeout = None if timeout is None else datetime.timedelta(seconds=timeout)
         self.comm = dwf.part_comm(self.exchange, self.allreduce)
 
     def neighbour(self, mu, side) -> int:
@@ -48,7 +54,10 @@ class TorchPartComm:
             reqs.append(dist.isend(torch.from_numpy(send[k]), peer, group=self.group, tag=k))
             reqs.append(dist.irecv(torch.from_numpy(recv[k]), peer, group=self.group, tag=k ^ 1))
         for r in reqs:
-            r.wait()
+            if self.timeout is None:
+                r.wait()
+            elif not r.wait(self.timeout):
+                raise TimeoutError("face message timed out")
 
     def allreduce(self, v):
         dist.all_reduce(torch.from_numpy(v), group=self.group)

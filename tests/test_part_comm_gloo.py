@@ -91,3 +91,46 @@ def test_callback_failure_is_reported():
     assert c.exchange(None, SP(), SP(), nb) == 1
     v = (ctypes.c_double * 1)(1.0)
     assert c.allreduce(None, v, 1) == 1
+
+
+def _lonely(rank, world, port, out):
+    import time
+
+    import torch.distributed as tdist
+
+    from paper_1101_0423_gb300 import dist as pdist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    tdist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        if rank == 0:
+            # rank 1 never takes part in the exchange (it failed before the collective step)
+            tc = pdist.TorchPartComm((2, 1, 1, 1), pdist.grid_coord(0, (2, 1, 1, 1)), timeout=2.0)
+            n = 64
+            send = [np.zeros(n, np.uint8) if k < 2 else None for k in range(8)]
+            recv = [np.zeros(n, np.uint8) if k < 2 else None for k in range(8)]
+            SP = ctypes.c_void_p * 8
+            sp = SP(*[x.ctypes.data if x is not None else None for x in send])
+            rp = SP(*[x.ctypes.data if x is not None else None for x in recv])
+            t0 = time.monotonic()
+            rc = tc.comm.exchange(None, sp, rp, (ctypes.c_size_t * 8)(*([n, n] + [0] * 6)))
+            out[0] = (rc, time.monotonic() - t0)
+        else:
+            time.sleep(8.0)
+    finally:
+        os._exit(0)  # no collective teardown: the peer left mid-protocol
+
+
+def test_exchange_with_a_failed_peer_times_out():
+    """A part whose neighbour failed before the exchange gets a failed callback (DWF_ECOMM in
+    the library) after the transport's timeout instead of waiting for ever."""
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_lonely, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(60)
+        rc, waited = out[0]
+        assert rc == 1 and waited < 7.0
