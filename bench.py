@@ -591,6 +591,10 @@ def main():
                     help="only the served sweep: 40 requests over all four lattices at 0.2..0.95 of capacity")
     ap.add_argument("--serve-requests", type=int, default=40,
                     help="requests per arrival-rate run of --serve (the sweep lasts about 12.5 x this / capacity)")
+    ap.add_argument("--serve-prec", choices=("bf16", "f16", "f32"), default="bf16",
+                    help="inner precision of the served solves (the served workload names bf16)")
+    ap.add_argument("--serve-fractions", default="0.2,0.4,0.6,0.8,0.95",
+                    help="arrival rates of --serve as fractions of the measured capacity")
     ap.add_argument("--odwf", action="store_true",
                     help="only the optimal-weights solve on 16^3x32x16 against the cosine weights")
     ap.add_argument("--apply-ccdag", type=int, default=0, metavar="N",
@@ -640,12 +644,13 @@ def main():
     if args.serve:
         from paper_1101_0423_gb300 import build as _b, dwf
         _b.build()
-        for row in serve_measure(args.serve_requests, SERVE_LATTICES_FULL, dwf.PREC_BF16,
-                                 [0.2, 0.4, 0.6, 0.8, 0.95], progress=True):
+        prec = {"bf16": dwf.PREC_BF16, "f16": dwf.PREC_F16, "f32": dwf.PREC_F32}[args.serve_prec]
+        fractions = [float(f) for f in args.serve_fractions.split(",")]
+        for row in serve_measure(args.serve_requests, SERVE_LATTICES_FULL, prec, fractions, progress=True):
             print(json.dumps({"metric": "served solves/s, p99 latency", "config": {
                 "workload": "served: uniform lattice {8^4,12^3x24,16^3x32,24^3x48} x Ns {8,16,24,32} x "
-                            "mq U[0.005,0.1] x {shamir,borici,cosine}, bf16 inner, tol 1e-10, 150 GB budget",
-                "requests": args.serve_requests}, **row}), flush=True)
+                            f"mq U[0.005,0.1] x {{shamir,borici,cosine}}, {args.serve_prec} inner, tol 1e-10, "
+                            "150 GB budget", "requests": args.serve_requests}, **row}), flush=True)
         return
 
     import numpy as np
