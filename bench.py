@@ -723,13 +723,16 @@ def main():
     params.profile = 0
     barrier()
     t0 = time.perf_counter()
-    e2e_flops = 0.0
+    e2e_flops, e2e_dev_ms, e2e_walls = 0.0, 0.0, []
     for _ in range(args.steps):
         st = dwf.SolveStats()
+        tw = time.perf_counter()
         rc = lib.dwf_solve(ctx.h, pe, pp, ctypes.byref(params), ctypes.byref(st))
+        e2e_walls.append(1e3 * (time.perf_counter() - tw))
         if rc != 0:
             raise dwf.DwfError(rc, dwf.dwf_last_error(ctx.h))
         e2e_flops += st.flops
+        e2e_dev_ms += st.time_ms
     barrier()
     e2e_s = time.perf_counter() - t0
     e2e_s, e2e_flops = aggregate_over_ranks(e2e_s, e2e_flops, device="cuda")
@@ -777,7 +780,8 @@ def main():
                    "iters": s0["iters"], "restarts": s0["restarts"], "true_res": s0["true_res"],
                    "true_res_full": s0["true_res_full"],
                    "solves_per_s": world * args.steps / (t_max * 1e-3)},
-        "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                "wall_ms_per_step": e2e_walls, "solve_device_ms_per_step": e2e_dev_ms / args.steps},
         "gpu_launches": launches,
         "roofline": roofline,
         "clocks": clocks,
