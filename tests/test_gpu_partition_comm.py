@@ -49,7 +49,7 @@ def _rank(rank, world, port, case, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     tdist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        dims, grid, ns, mq, kind, U, x, b, prm = case
+        dims, grid, ns, mq, kind, U, x, b, b0, prm, prm16 = case
         om, sg = inputs.weights(kind, ns)
         coord, sl = _blocks(dims, grid, ns)[rank]
         part = dwf.dwf_create_part(dims, grid, coord, ns, M0, mq, om, sg)
@@ -62,6 +62,8 @@ def _rank(rank, world, port, case, out):
                 res[(op, prec)] = dwf.dwf_part_apply_comm(part, tc.comm, op, prec, parity, _local(x, dims, ns, sl))
             sol, st = dwf.dwf_part_solve_comm(part, tc.comm, _local(b, dims, ns, sl), **prm)
             res["solve"] = (sol, st["iters"], st["restarts"], st["true_res_full"], st["converged"])
+            sol, st = dwf.dwf_part_solve_comm(part, tc.comm, _local(b0, dims, ns, sl), **prm16)
+            res["solve16"] = (sol, st["iters"], st["restarts"], st["true_res"], st["converged"])
             out[rank] = res
         finally:
             dwf.dwf_destroy(part)
@@ -76,13 +78,16 @@ def test_two_processes_one_part_each(gpu_lib, grid):
     U = inputs.gauge_field(dims, 0.5, seed=61)
     x = inputs.gaussian_source(dims, ns, seed=62)
     b = inputs.gaussian_source(dims, ns, seed=63)
+    b0 = inputs.gaussian_source(dims, ns, seed=64, parity=0)
     prm = {"inner_prec": dwf.PREC_F32, "tol": 1e-10}
+    # normal equations on the even sites with fp16 inner iterations (16-bit faces)
+    prm16 = {"inner_prec": dwf.PREC_F16, "tol": 1e-10, "system": dwf.SYS_NORMAL, "schur_parity": 0}
     world = int(np.prod(grid))
     ctx = mp.get_context("spawn")
     with ctx.Manager() as mgr:
         out = mgr.dict()
         port = _free_port()
-        case = (dims, grid, ns, mq, kind, U, x, b, prm)
+        case = (dims, grid, ns, mq, kind, U, x, b, b0, prm, prm16)
         procs = [ctx.Process(target=_rank, args=(r, world, port, case, out)) for r in range(world)]
         for p in procs:
             p.start()
@@ -114,6 +119,7 @@ def test_two_processes_one_part_each(gpu_lib, grid):
             tol = {dwf.PREC_F64: 1e-12, dwf.PREC_F32: 1e-5, dwf.PREC_F16: 5e-3}[prec]
             assert np.max(np.abs(got - want)) / np.max(np.abs(want)) <= tol
         sol_1p, st_1p = dwf.dwf_part_solve(parts, b, **prm)
+        sol16_1p, st16_1p = dwf.dwf_part_solve(parts, b0, **prm16)
     finally:
         for p in parts:
             dwf.dwf_destroy(p)
@@ -128,3 +134,14 @@ def test_two_processes_one_part_each(gpu_lib, grid):
     assert np.array_equal(sol, sol_1p)
     r = b - oracle.dfull(dims, ns, U, M0, mq, om, sg, sol)
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-10
+    g = np.zeros((dims[3], dims[2], dims[1], dims[0], ns, 24))
+    for r_, (_, sl) in enumerate(_blocks(dims, grid, ns)):
+        g[sl] = res[r_]["solve16"][0].reshape(g[sl].shape)
+    sol16 = g.reshape(-1)
+    for r_ in range(world):
+        _, iters, restarts, rres, conv = res[r_]["solve16"]
+        assert conv == 1 and iters == st16_1p["iters"] and restarts == st16_1p["restarts"]
+        assert rres == st16_1p["true_res"]
+    assert np.array_equal(sol16, sol16_1p)
+    r = b0 - oracle.ccdag_op(dims, ns, U, mp5, mm5, 0, sol16)
+    assert np.linalg.norm(r) / np.linalg.norm(b0) <= 1e-10

@@ -129,3 +129,29 @@ def test_ragged_rejects_bad_sets(gpu_lib):
     finally:
         for c in ctxs:
             c.close()
+
+
+def test_ragged_member_that_does_not_converge(gpu_lib):
+    """A heavy-mass member converges within max_iter (the oracle's FP64 CG on its normal
+    equations takes 151 iterations) while a light one does not (404): the set returns
+    DWF_ENOCONV, the converged member's solution is its single solve bit for bit (and meets
+    the oracle's residual), the other reports converged = 0."""
+    dwf = gpu_lib
+    dims = (4, 4, 4, 4)
+    U = inputs.gauge_field(dims, 0.5, seed=74)
+    members = [(8, 0.9, "shamir"), (8, 0.001, "shamir")]
+    rhs = [inputs.gaussian_source(dims, ns, seed=320 + k) for k, (ns, _, _) in enumerate(members)]
+    ctxs = _contexts(dwf, dims, U, members)
+    try:
+        with pytest.raises(dwf.DwfError) as e:
+            dwf.dwf_solve_ragged([c.h for c in ctxs], rhs, max_iter=250)
+        assert e.value.status == dwf.DWF_ENOCONV
+        sol, stats = dwf.dwf_solve_ragged([c.h for c in ctxs], rhs, max_iter=250, allow_noconv=True)
+        x0, s0 = dwf.dwf_solve(ctxs[0].h, rhs[0], max_iter=250)
+    finally:
+        for c in ctxs:
+            c.close()
+    assert stats[0]["converged"] == 1 and stats[1]["converged"] == 0
+    assert stats[0]["iters"] == s0["iters"] and np.array_equal(sol[0], x0)
+    om, sg = inputs.weights("shamir", 8)
+    assert relnorm(oracle.dfull(dims, 8, U, M0, 0.9, om, sg, sol[0]), rhs[0]) <= 1e-10
