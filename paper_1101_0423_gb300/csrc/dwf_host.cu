@@ -1731,13 +1731,18 @@ struct SolveRun {
         continue;
       }
       // Sec. 2.3: fall back to defect correction when the reliable updates stop converging
-      // (the true residual grew, or the inner recursion diverged or stalled)
+      // (the true residual grew, or the inner recursion diverged or stalled).  A 16-bit
+      // inner CG (a single solve) instead continues in FP32 with reliable updates at its
+      // first such cycle: measured at 16^3x32x16, every 16-bit solve whose cycle failed
+      // once failed again under 16-bit defect correction before reaching FP32 anyway
       const bool failed = R[k].rhat2 > R[k].prev_rhat2 || reason == RS_DIVERGED || reason == RS_STALLED;
-      if (prm.mode == DWF_MODE_AUTO && R[k].mode == DWF_MODE_RELIABLE && failed) {
+      const bool to_f32 = prm.mode == DWF_MODE_AUTO && failed && S.prec >= P_F16 && K == 1;
+      if (prm.mode == DWF_MODE_AUTO && R[k].mode == DWF_MODE_RELIABLE && failed && !to_f32) {
         R[k].mode = DWF_MODE_DEFECT;
-      } else if (prm.mode == DWF_MODE_AUTO && R[k].mode == DWF_MODE_DEFECT && failed && S.prec >= P_F16 && K == 1) {
+      } else if (to_f32) {
         // 16-bit storage is too coarse for this system: continue from x_hat with FP32
-        // inner iterations (the FP64 state x_hat, r_hat is untouched)
+        // inner iterations and reliable updates (the FP64 state x_hat, r_hat is untouched)
+        R[k].mode = DWF_MODE_RELIABLE;
         TRY(ensure_gauge(c, P_F32, st));
         S.prec = P_F32;
         if (!(prm.delta > 0.0)) delta = default_delta(P_F32);

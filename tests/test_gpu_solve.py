@@ -116,7 +116,7 @@ def test_full_size_config1_solve(gpu_lib):
     assert res <= 1e-10, f"oracle true residual {res:.3e}, stats {st}"
 
 
-def test_bf16_inner_escalates_to_fp32_when_defect_correction_stalls(gpu_lib):
+def test_bf16_inner_escalates_to_fp32_when_its_cycles_fail(gpu_lib):
     """16^3 x 32 x Ns=16 Borici, mq = 0.0064: bf16 inner iterations cannot contract at this
     conditioning; AUTO mode must finish with FP32 inner iterations and meet the residual."""
     from paper_1101_0423_gb300 import dwf
