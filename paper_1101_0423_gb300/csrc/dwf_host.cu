@@ -1484,6 +1484,7 @@ struct SolveRun {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   SolveState S;
   Field eta[2], etap[2], phi[2], psi[2], dpsi[2];
+  int eta_of = -1;  // the right-hand side whose eta and eta' the shared fields hold
   Slots sl;
   Geom g;
   size_t full_doubles = 0, nbytes64 = 0;
@@ -1519,8 +1520,11 @@ struct SolveRun {
     return DWF_OK;
   }
 
-  // eta'_k = S1 eta_k on both parities (the shared temporaries eta, etap)
+  // eta'_k = S1 eta_k on both parities (the shared temporaries eta, etap; nothing else
+  // writes them during the solve, so a single system's are formed once)
   dwf_status prep_eta(int k) {
+    if (eta_of == k) return DWF_OK;
+    eta_of = k;
     for (int p = 0; p < 2; ++p) {
       {
         Timed t(c, st, DWF_KC_F64);
