@@ -169,3 +169,20 @@ def test_server_struct_layouts_match_header(tmp_path):
     assert rq == ctypes.sizeof(dwf.Request) and off_p == dwf.Request.params.offset
     assert rs == ctypes.sizeof(dwf.Result)
     assert ss == ctypes.sizeof(dwf.ServerStats) and off_c == dwf.ServerStats.cancelled.offset
+
+
+def test_partition_struct_layouts_match_header(tmp_path):
+    """dwf_partition and dwf_part_comm (the domain decomposition's C structs) as the binding
+    lays them out."""
+    from paper_1101_0423_gb300 import dwf
+    src = tmp_path / "sz3.c"
+    src.write_text('#include "dwf.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(dwf_partition),'
+                   ' offsetof(dwf_partition, coord), sizeof(dwf_part_comm),'
+                   ' offsetof(dwf_part_comm, exchange), offsetof(dwf_part_comm, allreduce));return 0;}\n')
+    exe = tmp_path / "sz3"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    sp, off_coord, sc, off_ex, off_ar = map(int, subprocess.check_output([str(exe)]).split())
+    assert sp == ctypes.sizeof(dwf.Partition) and off_coord == dwf.Partition.coord.offset
+    assert sc == ctypes.sizeof(dwf.PartComm)
+    assert off_ex == dwf.PartComm.exchange.offset and off_ar == dwf.PartComm.allreduce.offset
