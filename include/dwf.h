@@ -426,6 +426,7 @@ typedef struct {
     long long batched;               /* requests that ran as rows of a shared batch */
 } dwf_server_stats;
 
+/* Fill p with the server defaults listed above (NULL is ignored). */
 void dwf_server_params_default(dwf_server_params *p);
 /* Create a server (no device work until a request runs).  params may be NULL. */
 dwf_status dwf_server_create(const dwf_server_params *params, dwf_server **out);
