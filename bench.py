@@ -771,6 +771,15 @@ def main():
                 "class_share": {k: cls_ms[k] / total for k in cls_ms},
                 "class_frac": {k: (alg[k] * n / (cls_ms[k] / max(cls_n[k], 1) * 1e-3) / 1e9) / peak
                                for k in alg if cls_n[k]}}
+    # the launch shapes the autotuner chose in this process for the timed solves
+    shapes = {}
+    for name, kc in (("hop_m5", dwf.KC_HOP_M5), ("hop_xpay", dwf.KC_HOP_XPAY), ("hop_update", dwf.KC_HOP_UPDATE)):
+        try:
+            t, pers, tuned = dwf.dwf_tuned_shape(ctx.h, prec, kc)
+            shapes[name] = {"threads": t, "persistent": bool(pers), "tuned": bool(tuned)}
+        except Exception:  # a shape report must not cost the line
+            pass
+    roofline["launch_shapes"] = shapes
 
     if rank != 0:
         if world > 1:
